@@ -1,0 +1,197 @@
+/*
+ * nbfd.h -- C ABI of libnbfd, a GB300 (sm_103a) decoder for (2,k)-regular non-binary LDPC
+ * codes over GF(2^m) using the Log-Fourier sum-product algorithm of Kasai & Sakaniwa,
+ * "Fourier Domain Decoding Algorithm of Non-Binary LDPC Codes for Parallel Implementation",
+ * IEICE Trans. Fundamentals 93(11), 2010.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - q = 2^m, 2 <= m <= 8. A field element is an integer in [0, q): bit i-1 is the coefficient
+ *   of alpha^(i-1) (Section 2, m-bit representation).
+ * - Edges are held in check-major order: library edge slot e = c*k + j is the j-th edge of
+ *   check c. nbfd_code_edge_order() maps slots back to the caller's edge indices.
+ * - Message vectors ("Gamma form", Section 3.2): one float32 per z in GF(2^m), laid out
+ *   [frame][edge][z] (or [frame][variable][z]), contiguous in z. The float's sign bit is the
+ *   GF(2) sign of P(z); its magnitude is -ln|P(z)| >= 0 (+inf when P(z) = 0). Every message the
+ *   library writes is normalised so that P(0) = 1 (stored as +0.0f).
+ * - Channel input: bit LLRs L = ln Pr(b=0|y)/Pr(b=1|y), float32 laid out [frame][variable][bit],
+ *   bit i-1 <-> coordinate of alpha^(i-1).
+ * - Pointers named *_dev are device pointers on the device current when the code was created;
+ *   the caller owns them and the library never frees them. Work is enqueued on `cuda_stream`
+ *   (a cudaStream_t; NULL = legacy default stream).
+ * - Every call returns an int status (NBFD_OK = 0 or a negative NBFD_E* code) and never throws;
+ *   nbfd_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef NBFD_H
+#define NBFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define NBFD_OK 0
+#define NBFD_EINVAL (-1)    /* bad argument (null pointer, size out of range, ...) */
+#define NBFD_ENOTREG (-2)   /* graph is not (2,k)-regular, or counts disagree */
+#define NBFD_EPOLY (-3)     /* polynomial not of degree m, or not primitive */
+#define NBFD_EDUP (-4)      /* a (check, variable) pair appears twice */
+#define NBFD_EZERO (-5)     /* an edge entry h_cv is 0 or >= q */
+#define NBFD_ENOMEM (-6)    /* host or device allocation failed / workspace too small */
+#define NBFD_ECUDA (-7)     /* a CUDA runtime call failed (message in nbfd_last_error) */
+#define NBFD_ETIMEDOUT (-8) /* a bounded device-side wait gave up */
+#define NBFD_EBUSY (-9)     /* over budget: retry later */
+#define NBFD_ENOTSUP (-10)  /* form / size not supported by this build */
+
+/* ---- variable-node convolution forms (Section 3.2, the boxplus definition) ----------- */
+#define NBFD_FORM_FP32_DIRECT 0 /* q^2-term signed sum of exponentials per output, FP32 */
+#define NBFD_FORM_BF16_HGEMM 1  /* Hadamard transforms on tensor cores, BF16 in / FP32 acc */
+#define NBFD_FORM_FP16_HGEMM 2  /* same, FP16 in / FP32 acc */
+#define NBFD_FORM_FP32_FWHT 3   /* fast Walsh-Hadamard butterflies, FP32 */
+
+typedef struct nbfd_code nbfd_code; /* opaque, library-owned, immutable after creation */
+
+/*
+ * nbfd_code_create -- load a (2,k)-regular code H = {h_cv} (Section 2: M x N over GF(2^m),
+ * column weight j = 2, row weight k, M = 2N/k).
+ *   N, M, k, m       : sizes; requires 2 <= m <= 8, 2 <= k <= 32, n_edges == 2N == M*k.
+ *   prim_poly        : primitive polynomial of alpha, bit j = coefficient of x^j (e.g. 0x11D).
+ *   edge_check/var/h : host arrays of n_edges entries, in any order: the edge (c, v) carries
+ *                      h_cv in [1, q). Copied; the caller keeps ownership.
+ *   out              : receives the handle (device tables are allocated on the current device).
+ * Errors: NBFD_EINVAL, NBFD_ENOTREG, NBFD_EPOLY, NBFD_EDUP, NBFD_EZERO, NBFD_ENOMEM, NBFD_ECUDA.
+ */
+int nbfd_code_create(int N, int M, int k, int m, uint32_t prim_poly, int n_edges,
+                     const int32_t *edge_check, const int32_t *edge_var, const uint16_t *edge_h,
+                     nbfd_code **out);
+
+/* Free a handle (NULL is ignored). No decode using it may be in flight. */
+void nbfd_code_destroy(nbfd_code *code);
+
+/* Sizes of a handle (any out pointer may be NULL). */
+int nbfd_code_info(const nbfd_code *code, int *N, int *M, int *k, int *m);
+
+/* caller_edge_of_slot[e] (host, n_edges entries) = index in the caller's edge arrays of library
+ * edge slot e (check-major order). */
+int nbfd_code_edge_order(const nbfd_code *code, int32_t *caller_edge_of_slot);
+
+/*
+ * nbfd_field_index_map -- host-only (no device work): the Fourier index map of GF(2^m) for the
+ * primitive polynomial prim_poly, table[h*q + z] = H z with H = (A^i)^T for h = alpha^i
+ * (Section 3.1 check-to-variable step; Appendix A). Row h = 0 is zero. `table` holds q*q bytes.
+ * Errors: NBFD_EINVAL (m outside [2, 8] or table NULL), NBFD_EPOLY.
+ */
+int nbfd_field_index_map(int m, uint32_t prim_poly, uint8_t *table);
+
+/* Host copy of the Fourier index map of Section 3.1 / Appendix A: table[h*q + z] = H z with
+ * H = (A^i)^T for h = alpha^i (row h = 0 is zero). `table` holds q*q bytes. */
+int nbfd_code_index_map(const nbfd_code *code, uint8_t *table);
+
+/*
+ * nbfd_decode_workspace_size -- bytes of device scratch that nbfd_decode needs for n_frames
+ * frames, max_iter iterations and the given form (messages in both directions, per-edge
+ * syndrome words, active-frame lists and counters).
+ */
+size_t nbfd_decode_workspace_size(const nbfd_code *code, int n_frames, int max_iter, int form);
+
+/*
+ * nbfd_decode -- full decoder of Section 2 (INITIALIZATION, then CHECK TO VARIABLE, VARIABLE TO
+ * CHECK and TENTATIVE DECISION repeated) with the Log-Fourier rules of Section 3.2:
+ *   INIT   Lambda0 = Gamma(WHT(p0)) from the bit LLRs, sent on both edges of every variable;
+ *   C->V   permute by H_cv, leave-one-out sum over the other k-1 edges, permute by H_cv^{-1};
+ *   V->C   Lambda0 [+] Lambda_c'v (boxplus log-convolution), normalised to P(0) = 1;
+ *   TENT.  bit i of x_hat_v = sign of M_v(alpha^{i-1}); Fourier syndrome bit i of check c =
+ *          XOR over V_c of the signs of M_v(H_cv alpha^{i-1}).
+ * A frame stops at iteration l (1 <= l <= max_iter) when all its Fourier syndrome bits are 0
+ * and the GF(2^m) syndrome of x_hat is 0; stopped frames are dropped from later iterations.
+ *   n_frames        : F >= 0 (F = 0 returns NBFD_OK without work).
+ *   llr_dev         : [F][N][m] float32 bit LLRs (device).
+ *   max_iter        : >= 1.
+ *   form            : NBFD_FORM_*.
+ *   symbols_dev     : [F][N] uint16 out: the last tentative decision of each frame.
+ *   syndrome_ok_dev : [F] uint8 out: 1 iff H x_hat = 0 for the output symbols.
+ *   iters_dev       : [F] int32 out: iteration at which the frame stopped (max_iter if never).
+ *   workspace_dev   : device scratch of >= nbfd_decode_workspace_size() bytes, 256-byte
+ *                     aligned; NULL makes the call allocate and free it on `cuda_stream`.
+ * The call is stream-ordered but synchronises with `cuda_stream` once per iteration to test
+ * for early termination (it returns after the last iteration's kernels completed).
+ * Errors: NBFD_EINVAL, NBFD_ENOTSUP, NBFD_ENOMEM, NBFD_ECUDA.
+ */
+int nbfd_decode(const nbfd_code *code, int n_frames, const float *llr_dev, int max_iter, int form,
+                uint16_t *symbols_dev, uint8_t *syndrome_ok_dev, int32_t *iters_dev,
+                void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+/* ---- step-level entry points (one step of Section 3.2 each, all frames, no early stop) -- */
+
+/*
+ * nbfd_init_messages -- INITIALIZATION of Section 3.2: p0_v(x) = prod_i Pr(b_i = x_i | y_i),
+ * P0_v = WHT(p0_v) (Section 2.1 definition, computed with butterflies), Lambda0_v = Gamma(P0_v)
+ * normalised to P0(0) = 1.
+ *   llr_dev     : [F][N][m] float32.
+ *   lambda0_dev : [F][N][q] float32 Gamma form out, or NULL.
+ *   v2c_dev     : [F][E][q] float32 out (Lambda0 of each slot's variable), or NULL.
+ */
+int nbfd_init_messages(const nbfd_code *code, int n_frames, const float *llr_dev,
+                       float *lambda0_dev, float *v2c_dev, void *cuda_stream);
+
+/*
+ * nbfd_check_update -- CHECK TO VARIABLE of Section 3.2 for every check of every frame:
+ * Lambda~_vc(z) = Lambda_vc(H_cv z); Lambda~_cv = Gamma-sum over the other k-1 edges (signs XOR,
+ * log-magnitudes add, computed without subtraction so +inf entries stay exact);
+ * Lambda_cv(z) = Lambda~_cv(H_cv^{-1} z).
+ *   v2c_dev : [F][E][q] in; c2v_dev : [F][E][q] out (must not alias v2c_dev).
+ */
+int nbfd_check_update(const nbfd_code *code, int n_frames, const float *v2c_dev, float *c2v_dev,
+                      void *cuda_stream);
+
+/*
+ * nbfd_var_update -- VARIABLE TO CHECK and TENTATIVE DECISION of Section 3.2 for every
+ * variable of every frame. The channel message Lambda0_v is recomputed from the LLRs with the
+ * same device code as nbfd_init_messages (it is not read from memory).
+ *   V->C: Lambda_vc = Lambda0_v [+] Lambda_c'v (c' the other check of v), normalised.
+ *   M_v  = Lambda0_v [+] Lambda_c1v [+] Lambda_c2v, evaluated at the 3m points it is needed at.
+ *   llr_dev      : [F][N][m] in.      c2v_dev : [F][E][q] in.
+ *   v2c_dev      : [F][E][q] out (must not alias c2v_dev).
+ *   symbols_dev  : [F][N] uint16 out, bit i-1 = sign bit of M_v(alpha^{i-1}) (or NULL).
+ *   fsyn_dev     : [F][E] uint8 out, bit i-1 = sign bit of M_v(H_cv alpha^{i-1}) for the edge's
+ *                  (c, v) (or NULL).
+ */
+int nbfd_var_update(const nbfd_code *code, int n_frames, int form, const float *llr_dev,
+                    const float *c2v_dev, float *v2c_dev, uint16_t *symbols_dev, uint8_t *fsyn_dev,
+                    void *cuda_stream);
+
+/*
+ * nbfd_syndrome -- syndromes of Section 3.1/3.2 for every check of every frame:
+ *   fourier_dev[f][c] = XOR over the k edges of c of fsyn_dev[f][e]  (Fourier-domain syndrome);
+ *   exact_dev[f][c]   = sum_{v in V_c} h_cv x_v over GF(2^m)          (x = symbols_dev[f]).
+ *   symbols_dev : [F][N] uint16 in; fsyn_dev : [F][E] uint8 in (may be NULL: fourier not
+ *   written); fourier_dev, exact_dev : [F][M] uint16 out (either may be NULL).
+ */
+int nbfd_syndrome(const nbfd_code *code, int n_frames, const uint16_t *symbols_dev,
+                  const uint8_t *fsyn_dev, uint16_t *fourier_dev, uint16_t *exact_dev,
+                  void *cuda_stream);
+
+/* ---- kernel timers (CUDA events around every launch of nbfd_decode) -------------------- */
+#define NBFD_KERNEL_INIT 0
+#define NBFD_KERNEL_CHECK 1
+#define NBFD_KERNEL_VAR 2
+#define NBFD_KERNEL_SYNDROME 3
+#define NBFD_KERNEL_COUNT 4
+
+/* Enable (1) or disable (0) the timers for the calling process; resets the totals. */
+int nbfd_prof_enable(int on);
+/* Totals since the last enable: device milliseconds, launches, and frame-units (the sum over
+ * launches of the number of frames the launch processed). Any out pointer may be NULL. */
+int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_units);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *nbfd_last_error(void);
+/* Static name of a status code. */
+const char *nbfd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBFD_H */

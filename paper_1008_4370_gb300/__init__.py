@@ -1,0 +1,233 @@
+"""GB300-native Log-Fourier sum-product decoder for (2,k)-regular non-binary LDPC codes.
+
+Python binding of libnbfd (include/nbfd.h): the functions below carry the C names and only
+marshal arguments -- every step of decoding runs in the library's CUDA kernels. Device buffers
+are torch CUDA tensors (contiguous, of the dtype the header states) or raw device addresses.
+The library is loaded on first use; if it has not been built the call raises instead of
+falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "NbfdError", "lib", "FORM_FP32_DIRECT", "FORM_BF16_HGEMM", "FORM_FP16_HGEMM", "FORM_FP32_FWHT",
+    "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
+    "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_init_messages",
+    "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
+    "nbfd_last_error", "nbfd_status_string", "Code", "decode",
+]
+
+FORM_FP32_DIRECT = 0
+FORM_BF16_HGEMM = 1
+FORM_FP16_HGEMM = 2
+FORM_FP32_FWHT = 3
+KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME = 0, 1, 2, 3
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libnbfd.so")
+
+# (name, restype, argtypes) of every exported symbol declared in include/nbfd.h
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = [
+    ("nbfd_code_create", _I, [_I, _I, _I, _I, ctypes.c_uint32, _I, _P, _P, _P, ctypes.POINTER(_P)]),
+    ("nbfd_code_destroy", None, [_P]),
+    ("nbfd_code_info", _I, [_P, _P, _P, _P, _P]),
+    ("nbfd_code_edge_order", _I, [_P, _P]),
+    ("nbfd_code_index_map", _I, [_P, _P]),
+    ("nbfd_field_index_map", _I, [_I, ctypes.c_uint32, _P]),
+    ("nbfd_decode_workspace_size", ctypes.c_size_t, [_P, _I, _I, _I]),
+    ("nbfd_decode", _I, [_P, _I, _P, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    ("nbfd_init_messages", _I, [_P, _I, _P, _P, _P, _P]),
+    ("nbfd_check_update", _I, [_P, _I, _P, _P, _P]),
+    ("nbfd_var_update", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
+    ("nbfd_syndrome", _I, [_P, _I, _P, _P, _P, _P, _P]),
+    ("nbfd_prof_enable", _I, [_I]),
+    ("nbfd_prof_get", _I, [_I, _P, _P, _P]),
+    ("nbfd_last_error", ctypes.c_char_p, []),
+    ("nbfd_status_string", ctypes.c_char_p, [_I]),
+]
+
+_lib = None
+
+
+class NbfdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libnbfd (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1008_4370_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise NbfdError(status, nbfd_last_error())
+
+
+def _dptr(t, dtype=None):
+    """Device address of a torch CUDA tensor (or pass an int / None through)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def nbfd_last_error() -> str:
+    return lib().nbfd_last_error().decode()
+
+
+def nbfd_status_string(status: int) -> str:
+    return lib().nbfd_status_string(status).decode()
+
+
+def nbfd_code_create(N, M, k, m, prim_poly, edge_check, edge_var, edge_h):
+    ec = np.ascontiguousarray(edge_check, dtype=np.int32)
+    ev = np.ascontiguousarray(edge_var, dtype=np.int32)
+    eh = np.ascontiguousarray(edge_h, dtype=np.uint16)
+    h = ctypes.c_void_p()
+    _check(lib().nbfd_code_create(int(N), int(M), int(k), int(m), int(prim_poly), len(ec),
+                                  ec.ctypes.data, ev.ctypes.data, eh.ctypes.data, ctypes.byref(h)))
+    return h.value
+
+
+def nbfd_code_destroy(handle):
+    lib().nbfd_code_destroy(handle)
+
+
+def nbfd_code_info(handle):
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(lib().nbfd_code_info(handle, *[ctypes.byref(v) for v in vals]))
+    return tuple(v.value for v in vals)
+
+
+def nbfd_code_edge_order(handle, n_edges):
+    out = np.empty(n_edges, dtype=np.int32)
+    _check(lib().nbfd_code_edge_order(handle, out.ctypes.data))
+    return out
+
+
+def nbfd_code_index_map(handle, q):
+    out = np.empty((q, q), dtype=np.uint8)
+    _check(lib().nbfd_code_index_map(handle, out.ctypes.data))
+    return out
+
+
+def nbfd_field_index_map(m, prim_poly):
+    q = 1 << int(m)
+    out = np.empty((q, q), dtype=np.uint8)
+    _check(lib().nbfd_field_index_map(int(m), int(prim_poly), out.ctypes.data))
+    return out
+
+
+def nbfd_decode_workspace_size(handle, n_frames, max_iter, form):
+    return int(lib().nbfd_decode_workspace_size(handle, int(n_frames), int(max_iter), int(form)))
+
+
+def nbfd_decode(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, iters,
+                workspace=None, workspace_bytes=0, stream=None):
+    import torch
+    _check(lib().nbfd_decode(handle, int(n_frames), _dptr(llr, torch.float32), int(max_iter), int(form),
+                             _dptr(symbols),
+                             _dptr(syndrome_ok, torch.uint8), _dptr(iters, torch.int32),
+                             _dptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def nbfd_init_messages(handle, n_frames, llr, lambda0, v2c, stream=None):
+    _check(lib().nbfd_init_messages(handle, int(n_frames), _dptr(llr), _dptr(lambda0), _dptr(v2c),
+                                    _stream(stream)))
+
+
+def nbfd_check_update(handle, n_frames, v2c, c2v, stream=None):
+    _check(lib().nbfd_check_update(handle, int(n_frames), _dptr(v2c), _dptr(c2v), _stream(stream)))
+
+
+def nbfd_var_update(handle, n_frames, form, llr, c2v, v2c, symbols=None, fsyn=None, stream=None):
+    _check(lib().nbfd_var_update(handle, int(n_frames), int(form), _dptr(llr), _dptr(c2v), _dptr(v2c),
+                                 _dptr(symbols), _dptr(fsyn), _stream(stream)))
+
+
+def nbfd_syndrome(handle, n_frames, symbols, fsyn, fourier, exact, stream=None):
+    _check(lib().nbfd_syndrome(handle, int(n_frames), _dptr(symbols), _dptr(fsyn), _dptr(fourier),
+                               _dptr(exact), _stream(stream)))
+
+
+def nbfd_prof_enable(on: bool):
+    _check(lib().nbfd_prof_enable(1 if on else 0))
+
+
+def nbfd_prof_get(kernel: int):
+    ms = ctypes.c_double()
+    launches = ctypes.c_longlong()
+    units = ctypes.c_longlong()
+    _check(lib().nbfd_prof_get(int(kernel), ctypes.byref(ms), ctypes.byref(launches), ctypes.byref(units)))
+    return ms.value, launches.value, units.value
+
+
+class Code:
+    """Owner of an nbfd_code handle built from a code dict (N, M, k, m, poly, edge arrays)."""
+
+    def __init__(self, code: dict):
+        self.N, self.M, self.k, self.m = int(code["N"]), int(code["M"]), int(code["k"]), int(code["m"])
+        self.q = 1 << self.m
+        self.E = 2 * self.N
+        self.handle = nbfd_code_create(self.N, self.M, self.k, self.m, int(code["poly"]),
+                                       code["edge_check"], code["edge_var"], code["edge_h"])
+
+    def close(self):
+        if self.handle:
+            nbfd_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decode(code: Code, llr, max_iter: int, form: int = FORM_FP32_DIRECT, workspace=None, stream=None):
+    """Allocate outputs (torch, on llr's device) and run nbfd_decode; returns (symbols, ok, iters)."""
+    import torch
+    F = int(llr.shape[0])
+    dev = llr.device
+    sym = torch.empty((F, code.N), dtype=torch.int16, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    it = torch.empty(F, dtype=torch.int32, device=dev)
+    need = nbfd_decode_workspace_size(code.handle, F, max_iter, form)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    nbfd_decode(code.handle, F, llr, max_iter, form, sym.data_ptr(), ok, it, workspace, workspace.numel(),
+                stream)
+    return sym, ok, it

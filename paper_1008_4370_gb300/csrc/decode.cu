@@ -1,0 +1,280 @@
+// C ABI entry points that run kernels: the decoding loop (Section 2's four steps with the
+// Log-Fourier rules of Section 3.2), the step-level calls and the kernel timers.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "nbfd_internal.h"
+
+using namespace nbfd;
+
+namespace {
+
+// ---- kernel timers ------------------------------------------------------------------------
+struct ProfTotals {
+  double ms[NBFD_KERNEL_COUNT] = {};
+  long long launches[NBFD_KERNEL_COUNT] = {};
+  long long units[NBFD_KERNEL_COUNT] = {};
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+ProfTotals g_prof;
+
+struct PendingTimer {
+  int kernel;
+  long long units;
+  cudaEvent_t a, b;
+};
+
+class Timers {
+ public:
+  explicit Timers(bool on) : on_(on) {}
+  ~Timers() {
+    flush();
+    for (auto &e : pool_) cudaEventDestroy(e);
+  }
+  void begin(int kernel, long long units, cudaStream_t s) {
+    if (!on_) return;
+    cur_ = {kernel, units, get(), get()};
+    cudaEventRecord(cur_.a, s);
+  }
+  void end(cudaStream_t s) {
+    if (!on_) return;
+    cudaEventRecord(cur_.b, s);
+    pending_.push_back(cur_);
+  }
+  // Accumulate completed timers (the caller has synchronised the stream).
+  void flush() {
+    if (!on_ || pending_.empty()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : pending_) {
+      float ms = 0.0f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        g_prof.ms[p.kernel] += ms;
+        g_prof.launches[p.kernel] += 1;
+        g_prof.units[p.kernel] += p.units;
+      }
+      pool_.push_back(p.a);
+      pool_.push_back(p.b);
+    }
+    pending_.clear();
+  }
+
+ private:
+  cudaEvent_t get() {
+    if (!pool_.empty()) {
+      cudaEvent_t e = pool_.back();
+      pool_.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  bool on_;
+  PendingTimer cur_{};
+  std::vector<PendingTimer> pending_;
+  std::vector<cudaEvent_t> pool_;
+};
+
+// ---- workspace layout ----------------------------------------------------------------------
+struct Workspace {
+  float *v2c, *c2v;
+  uint8_t *fsyn;
+  int32_t *list[2];
+  int32_t *count;  // [max_iter + 2]
+  int32_t *stats;  // [16]
+  size_t bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Workspace carve(const nbfd_code *c, int F, int max_iter, char *base) {
+  Workspace w{};
+  const size_t msg = align256((size_t)F * c->E * c->q * sizeof(float));
+  size_t off = 0;
+  w.v2c = reinterpret_cast<float *>(base + off);
+  off += msg;
+  w.c2v = reinterpret_cast<float *>(base + off);
+  off += msg;
+  w.fsyn = reinterpret_cast<uint8_t *>(base + off);
+  off += align256((size_t)F * c->E);
+  w.list[0] = reinterpret_cast<int32_t *>(base + off);
+  off += align256((size_t)F * 4);
+  w.list[1] = reinterpret_cast<int32_t *>(base + off);
+  off += align256((size_t)F * 4);
+  w.count = reinterpret_cast<int32_t *>(base + off);
+  off += align256((size_t)(max_iter + 2) * 4);
+  w.stats = reinterpret_cast<int32_t *>(base + off);
+  off += align256(16 * 4);
+  w.bytes = off;
+  return w;
+}
+
+int check_device(const nbfd_code *c) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != c->device)
+    return set_error(NBFD_EINVAL, "current device %d differs from the code's device %d", dev,
+                     c->device);
+  return NBFD_OK;
+}
+
+}  // namespace
+
+extern "C" int nbfd_prof_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  g_prof = ProfTotals{};
+  return NBFD_OK;
+}
+
+extern "C" int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *units) {
+  if (kernel < 0 || kernel >= NBFD_KERNEL_COUNT) return set_error(NBFD_EINVAL, "bad kernel id");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (ms) *ms = g_prof.ms[kernel];
+  if (launches) *launches = g_prof.launches[kernel];
+  if (units) *units = g_prof.units[kernel];
+  return NBFD_OK;
+}
+
+extern "C" size_t nbfd_decode_workspace_size(const nbfd_code *c, int n_frames, int max_iter,
+                                             int form) {
+  (void)form;
+  if (!c || n_frames < 0 || max_iter < 0) return 0;
+  return carve(c, n_frames, max_iter, nullptr).bytes;
+}
+
+extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
+                           uint16_t *symbols, uint8_t *ok, int32_t *iters, void *workspace,
+                           size_t workspace_bytes, void *stream_) {
+  if (!c) return set_error(NBFD_EINVAL, "code is NULL");
+  if (F < 0) return set_error(NBFD_EINVAL, "n_frames < 0");
+  if (max_iter < 1) return set_error(NBFD_EINVAL, "max_iter must be >= 1");
+  if (!form_supported(form, c->m)) return set_error(NBFD_ENOTSUP, "form %d not supported", form);
+  if (F == 0) return NBFD_OK;
+  if (!llr || !symbols || !ok || !iters) return set_error(NBFD_EINVAL, "NULL buffer");
+  if (int st = check_device(c)) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream_);
+  const size_t need = nbfd_decode_workspace_size(c, F, max_iter, form);
+  bool owned = false;
+  if (workspace == nullptr) {
+    if (int st = check_cuda(cudaMallocAsync(&workspace, need, s), "cudaMallocAsync(workspace)"))
+      return st;
+    owned = true;
+  } else if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+    return set_error(NBFD_ENOMEM, "workspace of %zu bytes (need %zu, 256-byte aligned)",
+                     workspace_bytes, need);
+  }
+  Workspace w = carve(c, F, max_iter, static_cast<char *>(workspace));
+  int32_t *host_count = nullptr;
+  int st = NBFD_OK;
+  bool prof_on;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_on = g_prof_on;
+  }
+  Timers tm(prof_on);
+  do {
+    if ((st = check_cuda(cudaMallocHost(&host_count, sizeof(int32_t)), "cudaMallocHost"))) break;
+    if ((st = check_cuda(cudaMemsetAsync(w.count, 0, (size_t)(max_iter + 2) * 4 + 0, s),
+                         "cudaMemsetAsync")))
+      break;
+    if ((st = check_cuda(cudaMemsetAsync(w.stats, 0, 64, s), "cudaMemsetAsync"))) break;
+    if ((st = check_cuda(cudaMemsetAsync(ok, 0, (size_t)F, s), "cudaMemsetAsync"))) break;
+    // INITIALIZATION (+ list of iteration 1 = all frames, count[1] = F)
+    tm.begin(NBFD_KERNEL_INIT, F, s);
+    if ((st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s),
+                         "init kernel")))
+      break;
+    tm.end(s);
+    long long active = F;
+    for (int it = 1; it <= max_iter && active > 0; ++it) {
+      FrameSet fs;
+      fs.list = w.list[it & 1];
+      fs.count = w.count + it;
+      fs.n_static = F;
+      tm.begin(NBFD_KERNEL_CHECK, active, s);
+      if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s), "check kernel"))) break;
+      tm.end(s);
+      tm.begin(NBFD_KERNEL_VAR, active, s);
+      if ((st = check_cuda(launch_var(c, fs, form, llr, w.c2v, w.v2c, symbols, w.fsyn, s),
+                           "variable kernel")))
+        break;
+      tm.end(s);
+      tm.begin(NBFD_KERNEL_SYNDROME, active, s);
+      if ((st = check_cuda(launch_stop(c, fs, symbols, w.fsyn, it, max_iter, w.list[(it + 1) & 1],
+                                       w.count + it + 1, ok, iters, w.stats, s),
+                           "stop kernel")))
+        break;
+      tm.end(s);
+      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.count + it + 1, sizeof(int32_t),
+                                           cudaMemcpyDeviceToHost, s),
+                           "cudaMemcpyAsync(count)")))
+        break;
+      if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
+      tm.flush();
+      active = *host_count;
+    }
+  } while (false);
+  tm.flush();
+  if (host_count) cudaFreeHost(host_count);
+  if (owned) cudaFreeAsync(workspace, s);
+  return st;
+}
+
+// ---- step-level entry points ----------------------------------------------------------------
+
+extern "C" int nbfd_init_messages(const nbfd_code *c, int F, const float *llr, float *lambda0,
+                                  float *v2c, void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (F == 0) return NBFD_OK;
+  if (!llr) return set_error(NBFD_EINVAL, "llr is NULL");
+  if (int st = check_device(c)) return st;
+  return check_cuda(launch_init(c, F, llr, lambda0, v2c, nullptr, nullptr,
+                                static_cast<cudaStream_t>(stream)),
+                    "init kernel");
+}
+
+extern "C" int nbfd_check_update(const nbfd_code *c, int F, const float *v2c, float *c2v,
+                                 void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (F == 0) return NBFD_OK;
+  if (!v2c || !c2v || v2c == c2v) return set_error(NBFD_EINVAL, "bad message buffers");
+  if (int st = check_device(c)) return st;
+  FrameSet fs;
+  fs.n_static = F;
+  return check_cuda(launch_check(c, fs, v2c, c2v, static_cast<cudaStream_t>(stream)),
+                    "check kernel");
+}
+
+extern "C" int nbfd_var_update(const nbfd_code *c, int F, int form, const float *llr,
+                               const float *c2v, float *v2c, uint16_t *symbols, uint8_t *fsyn,
+                               void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (!form_supported(form, c->m)) return set_error(NBFD_ENOTSUP, "form %d not supported", form);
+  if (F == 0) return NBFD_OK;
+  if (!llr || !c2v || !v2c || v2c == c2v) return set_error(NBFD_EINVAL, "bad buffers");
+  if (int st = check_device(c)) return st;
+  FrameSet fs;
+  fs.n_static = F;
+  return check_cuda(launch_var(c, fs, form, llr, c2v, v2c, symbols, fsyn,
+                               static_cast<cudaStream_t>(stream)),
+                    "variable kernel");
+}
+
+extern "C" int nbfd_syndrome(const nbfd_code *c, int F, const uint16_t *symbols,
+                             const uint8_t *fsyn, uint16_t *fourier, uint16_t *exact,
+                             void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (F == 0) return NBFD_OK;
+  if (!symbols) return set_error(NBFD_EINVAL, "symbols is NULL");
+  if (fourier && !fsyn) return set_error(NBFD_EINVAL, "fourier output needs fsyn");
+  if (int st = check_device(c)) return st;
+  return check_cuda(launch_syndrome(c, F, symbols, fsyn, fourier, exact,
+                                    static_cast<cudaStream_t>(stream)),
+                    "syndrome kernel");
+}

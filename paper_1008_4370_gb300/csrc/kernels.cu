@@ -1,0 +1,517 @@
+// Kernels of one Log-Fourier decoding iteration (Section 3.2) on sm_103a.
+//
+//   k_init        INITIALIZATION: p0 from bit LLRs, transform with butterflies, Gamma form.
+//   k_check       CHECK TO VARIABLE: gather through H_cv, leave-one-out Gamma sums over the
+//                 other k-1 edges, scatter through H_cv^{-1}; staged in shared memory.
+//   k_var_direct  VARIABLE TO CHECK (boxplus of the channel message with the other check's
+//                 message, as q^2 signed products in FP32) + TENTATIVE DECISION (bits and
+//                 Fourier syndrome words from M_v at 3m points).
+//   k_syndrome    Fourier-domain and GF(2^m) syndromes per check.
+//   k_stop        per-frame stop test of one decoding iteration + compaction of active frames.
+//
+// Layouts: messages [frame][slot][z] float32 (Gamma form, see device_common.cuh), slots
+// check-major (slot = c*k + j); LLRs [frame][variable][bit].
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "nbfd_internal.h"
+
+namespace nbfd {
+
+template <int N>
+__device__ __forceinline__ void store_vec(float *dst, const float (&v)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4)
+      *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+  } else if constexpr (N == 2) {
+    *reinterpret_cast<float2 *>(dst) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) dst[j] = v[j];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_vec(float (&v)[N], const float *src) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+      const float4 x = *reinterpret_cast<const float4 *>(src + j);
+      v[j] = x.x;
+      v[j + 1] = x.y;
+      v[j + 2] = x.z;
+      v[j + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = src[j];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_vec_global(float (&v)[N], const float *__restrict__ src) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+      const float4 x = __ldg(reinterpret_cast<const float4 *>(src + j));
+      v[j] = x.x;
+      v[j + 1] = x.y;
+      v[j + 2] = x.z;
+      v[j + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = __ldg(src + j);
+  }
+}
+
+__device__ __forceinline__ int frame_count(const FrameSet &fs) {
+  return fs.list ? __ldg(fs.count) : fs.n_static;
+}
+__device__ __forceinline__ int frame_at(const FrameSet &fs, long long slot) {
+  return fs.list ? __ldg(fs.list + slot) : static_cast<int>(slot);
+}
+
+// ---------------------------------------------------------------------------------------
+// INITIALIZATION
+// ---------------------------------------------------------------------------------------
+template <int MB>
+__global__ void __launch_bounds__(256)
+    k_init(const float *__restrict__ llr, float *__restrict__ lambda0, float *__restrict__ v2c,
+           const int32_t *__restrict__ var_edges, int N, int E, int F, int32_t *list_out,
+           int32_t *count_out) {
+  using CL = ChannelLayout<MB>;
+  constexpr int Q = CL::Q, VPT = CL::VPT;
+  const int lane = threadIdx.x & 31, sub = lane / CL::LPV, l = lane % CL::LPV;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  if (list_out) {
+    for (long long i = gtid; i < F; i += nthr) list_out[i] = static_cast<int32_t>(i);
+    if (gtid == 0) *count_out = F;
+  }
+  const long long total = (long long)F * N;
+  for (long long base = (gtid >> 5) * CL::VPW; base < total; base += (nthr >> 5) * CL::VPW) {
+    const long long item = base + sub;
+    const bool valid = item < total;
+    const long long ic = valid ? item : total - 1;
+    float P[VPT];
+    channel_fourier<MB>(llr + ic * MB, l, P);
+    const float p0 = __shfl_sync(kFull, P[0], sub * CL::LPV);
+    float g[VPT];
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) g[j] = gamma_encode(P[j] / p0);
+    if (valid) {
+      if (lambda0) store_vec<VPT>(lambda0 + item * Q + l * VPT, g);
+      if (v2c) {
+        const long long f = item / N;
+        const int v = static_cast<int>(item - f * N);
+        const int e1 = __ldg(var_edges + 2 * v), e2 = __ldg(var_edges + 2 * v + 1);
+        store_vec<VPT>(v2c + ((size_t)f * E + e1) * Q + l * VPT, g);
+        store_vec<VPT>(v2c + ((size_t)f * E + e2) * Q + l * VPT, g);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// CHECK TO VARIABLE
+// ---------------------------------------------------------------------------------------
+// 256 threads = IPB checks x Q entries. A check's k slots are contiguous ([slot][z]), so the
+// IPB checks are staged with 16-byte loads; thread (check i, z) gathers V->C entry H_e z of
+// every slot e, forms the leave-one-out sums with a prefix and a suffix pass (no subtraction,
+// so +inf magnitudes stay exact), and writes output z' = H_e z of slot e in place: for each
+// slot, z -> H_e z is a bijection, so every shared word is read and written by one thread only.
+template <int MB, int KMAX>
+__global__ void __launch_bounds__(256)
+    k_check(const float *__restrict__ v2c, float *__restrict__ c2v,
+            const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
+            int E, FrameSet fs) {
+  constexpr int Q = 1 << MB;
+  constexpr int IPB = 256 / Q;
+  extern __shared__ float4 sm4[];
+  float *sm = reinterpret_cast<float *>(sm4);
+  const long long total = (long long)frame_count(fs) * M;
+  const int it = threadIdx.x / Q, z = threadIdx.x % Q;
+  const int kq4 = k * Q / 4;
+  for (long long base = (long long)blockIdx.x * IPB; base < total;
+       base += (long long)gridDim.x * IPB) {
+    for (int idx = threadIdx.x; idx < IPB * kq4; idx += blockDim.x) {
+      const int i = idx / kq4, r = idx - i * kq4;
+      const long long item = base + i;
+      if (item < total) {
+        const long long slot = item / M;
+        const int c = static_cast<int>(item - slot * M);
+        const int f = frame_at(fs, slot);
+        const float4 *src =
+            reinterpret_cast<const float4 *>(v2c + ((size_t)f * E + (size_t)c * k) * Q);
+        sm4[idx] = __ldg(src + r);
+      }
+    }
+    __syncthreads();
+    const long long item = base + it;
+    if (item < total) {
+      const int c = static_cast<int>(item % M);
+      float *s = sm + (size_t)it * k * Q;
+      float mag[KMAX];
+      uint32_t sg[KMAX];
+      int pos[KMAX];
+      uint32_t sx = 0;
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) {
+        if (e < k) {
+          const int h = __ldg(edge_h + (size_t)c * k + e);
+          pos[e] = __ldg(perm + h * Q + z);
+          const float x = s[e * Q + pos[e]];
+          mag[e] = fabsf(x);
+          sg[e] = __float_as_uint(x) & 0x80000000u;
+          sx ^= sg[e];
+        }
+      }
+      float suf[KMAX];
+      float run = 0.0f;
+#pragma unroll
+      for (int e = KMAX - 1; e >= 0; --e) {
+        if (e < k) {
+          suf[e] = run;
+          run += mag[e];
+        }
+      }
+      float pre = 0.0f;
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) {
+        if (e < k) {
+          const float o = pre + suf[e];
+          pre += mag[e];
+          s[e * Q + pos[e]] = __uint_as_float(__float_as_uint(o) | (sx ^ sg[e]));
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < IPB * kq4; idx += blockDim.x) {
+      const int i = idx / kq4, r = idx - i * kq4;
+      const long long item = base + i;
+      if (item < total) {
+        const long long slot = item / M;
+        const int c = static_cast<int>(item - slot * M);
+        const int f = frame_at(fs, slot);
+        float4 *dst = reinterpret_cast<float4 *>(c2v + ((size_t)f * E + (size_t)c * k) * Q);
+        dst[r] = sm4[idx];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// VARIABLE TO CHECK + TENTATIVE DECISION, FP32 direct form
+// ---------------------------------------------------------------------------------------
+// A group of TPV = Q/R lanes handles one variable; lane t owns the R outputs z = t*R + j.
+// U1 = P0 (*) C2 and U2 = P0 (*) C1 (XOR convolution, U(z) = sum_z1 P0(z1) C(z ^ z1)) are
+// accumulated as R x R XOR outer products of 16-byte shared-memory blocks, so each step does
+// 2R^2 FMAs for 3R loads. M_v = U1 (*) C1 is then evaluated only at the 3m points the bit and
+// syndrome read-out needs.
+template <int MB>
+__global__ void __launch_bounds__(256)
+    k_var_direct(const float *__restrict__ llr, const float *__restrict__ c2v,
+                 float *__restrict__ v2c, uint16_t *__restrict__ sym,
+                 uint8_t *__restrict__ fsyn, const int32_t *__restrict__ var_edges,
+                 const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int N,
+                 int E, FrameSet fs) {
+  using CL = ChannelLayout<MB>;
+  constexpr int Q = 1 << MB;
+  constexpr int R = Q < 8 ? Q : 8;
+  constexpr int TPV = Q / R;
+  constexpr int VPW = 32 / TPV;
+  constexpr int LOG_R = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  __shared__ __align__(16) float sm[8][3][VPW * Q];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / TPV, t = lane % TPV;
+  float *sa_w = sm[wib][0];
+  float *sa = sm[wib][0] + g * Q;
+  float *sc1 = sm[wib][1] + g * Q;
+  float *sc2 = sm[wib][2] + g * Q;
+  const long long total = (long long)frame_count(fs) * N;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = gw * VPW; base < total; base += nw * VPW) {
+    // channel message P0 (linear, P0(0) = 1) of the warp's VPW variables
+#pragma unroll
+    for (int r = 0; r < VPW / CL::VPW; ++r) {
+      const int gi = r * CL::VPW + lane / CL::LPV;
+      long long item = base + gi;
+      if (item >= total) item = total - 1;
+      const long long slot = item / N;
+      const int v = static_cast<int>(item - slot * N);
+      const int f = frame_at(fs, slot);
+      float P[CL::VPT];
+      channel_fourier<MB>(llr + ((size_t)f * N + v) * MB, lane % CL::LPV, P);
+      const float p0 = __shfl_sync(kFull, P[0], (lane / CL::LPV) * CL::LPV);
+#pragma unroll
+      for (int j = 0; j < CL::VPT; ++j)
+        sa_w[gi * Q + (lane % CL::LPV) * CL::VPT + j] = P[j] / p0;
+    }
+    const long long item = base + g;
+    const bool valid = item < total;
+    const long long ic = valid ? item : total - 1;
+    const long long slot = ic / N;
+    const int v = static_cast<int>(ic - slot * N);
+    const int f = frame_at(fs, slot);
+    const int e1 = __ldg(var_edges + 2 * v), e2 = __ldg(var_edges + 2 * v + 1);
+    {
+      float x1[R], x2[R];
+      load_vec_global<R>(x1, c2v + ((size_t)f * E + e1) * Q + t * R);
+      load_vec_global<R>(x2, c2v + ((size_t)f * E + e2) * Q + t * R);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        x1[j] = gamma_decode(x1[j]);
+        x2[j] = gamma_decode(x2[j]);
+      }
+      store_vec<R>(sc1 + t * R, x1);
+      store_vec<R>(sc2 + t * R, x2);
+    }
+    __syncwarp();
+    float u1[R], u2[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) u1[j] = u2[j] = 0.0f;
+#pragma unroll 4
+    for (int b = 0; b < TPV; ++b) {
+      float av[R], c1v[R], c2v_[R];
+      load_vec<R>(av, sa + b * R);
+      load_vec<R>(c1v, sc1 + (t ^ b) * R);
+      load_vec<R>(c2v_, sc2 + (t ^ b) * R);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          u1[j] = fmaf(av[i], c2v_[i ^ j], u1[j]);
+          u2[j] = fmaf(av[i], c1v[i ^ j], u2[j]);
+        }
+      }
+    }
+    const float n1 = __shfl_sync(kFull, u1[0], g * TPV);
+    const float n2 = __shfl_sync(kFull, u2[0], g * TPV);
+    if (valid) {
+      float o1[R], o2[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        o1[j] = gamma_encode(u1[j] / n1);
+        o2[j] = gamma_encode(u2[j] / n2);
+      }
+      store_vec<R>(v2c + ((size_t)f * E + e1) * Q + t * R, o1);  // excludes check of e1
+      store_vec<R>(v2c + ((size_t)f * E + e2) * Q + t * R, o2);  // excludes check of e2
+    }
+    // TENTATIVE: M(z) = sum_z1 U1(z1) C1(z ^ z1) at z = alpha^{i-1}, H_e1 alpha^{i-1},
+    // H_e2 alpha^{i-1}. Lane t holds U1 on its block; C1 is read from shared memory.
+    const int h1 = __ldg(edge_h + e1), h2 = __ldg(edge_h + e2);
+    uint32_t bits = 0, w1 = 0, w2 = 0;
+    const uint32_t neg1 = n1 < 0.0f ? 1u : 0u;
+#pragma unroll 1
+    for (int i = 0; i < MB; ++i) {
+#pragma unroll
+      for (int kind = 0; kind < 3; ++kind) {
+        const int zp = kind == 0 ? (1 << i) : __ldg(perm + (kind == 1 ? h1 : h2) * Q + (1 << i));
+        const int zb = zp >> LOG_R, zl = zp & (R - 1);
+        const float *cb = sc1 + (t ^ zb) * R;
+        float part = 0.0f;
+#pragma unroll
+        for (int j = 0; j < R; ++j) part = fmaf(u1[j], cb[j ^ zl], part);
+#pragma unroll
+        for (int o = TPV / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+        const uint32_t bit = (part < 0.0f ? 1u : 0u) ^ neg1;
+        if (kind == 0) bits |= bit << i;
+        else if (kind == 1) w1 |= bit << i;
+        else w2 |= bit << i;
+      }
+    }
+    if (valid && t == 0) {
+      if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(bits);
+      if (fsyn) {
+        fsyn[(size_t)f * E + e1] = static_cast<uint8_t>(w1);
+        fsyn[(size_t)f * E + e2] = static_cast<uint8_t>(w2);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// syndromes
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int gf_mul(int h, int x, const uint8_t *gexp, const uint8_t *glog) {
+  return x == 0 ? 0 : gexp[glog[h] + glog[x]];
+}
+
+__global__ void k_syndrome(const uint16_t *__restrict__ sym, const uint8_t *__restrict__ fsyn,
+                           uint16_t *__restrict__ fourier, uint16_t *__restrict__ exact,
+                           const int32_t *__restrict__ edge_var, const uint8_t *__restrict__ edge_h,
+                           const uint8_t *__restrict__ gexp, const uint8_t *__restrict__ glog,
+                           int N, int M, int k, int E, int F) {
+  const long long total = (long long)F * M;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long f = idx / M;
+    const int c = static_cast<int>(idx - f * M);
+    int fsv = 0, esv = 0;
+    for (int j = 0; j < k; ++j) {
+      const int e = c * k + j;
+      if (fsyn) fsv ^= fsyn[f * E + e];
+      esv ^= gf_mul(edge_h[e], sym[f * N + edge_var[e]], gexp, glog);
+    }
+    if (fourier) fourier[idx] = static_cast<uint16_t>(fsv);
+    if (exact) exact[idx] = static_cast<uint16_t>(esv);
+  }
+}
+
+// One block per active frame: the frame stops when every check's Fourier-domain syndrome word
+// and GF(2^m) syndrome are 0 (or at max_iter); otherwise it is appended to next_list.
+__global__ void __launch_bounds__(128)
+    k_stop(FrameSet fs, const uint16_t *__restrict__ sym, const uint8_t *__restrict__ fsyn,
+           const int32_t *__restrict__ edge_var, const uint8_t *__restrict__ edge_h,
+           const uint8_t *__restrict__ gexp_g, const uint8_t *__restrict__ glog_g, int q, int N,
+           int M, int k, int E, int iter, int max_iter, int32_t *__restrict__ next_list,
+           int32_t *__restrict__ next_count, uint8_t *__restrict__ ok, int32_t *__restrict__ iters,
+           int32_t *__restrict__ stats) {
+  __shared__ uint8_t gexp[512];
+  __shared__ uint8_t glog[256];
+  for (int i = threadIdx.x; i < 2 * q; i += blockDim.x) gexp[i] = gexp_g[i];
+  for (int i = threadIdx.x; i < q; i += blockDim.x) glog[i] = glog_g[i];
+  __syncthreads();
+  const int nf = frame_count(fs);
+  for (int s = blockIdx.x; s < nf; s += gridDim.x) {
+    const int f = frame_at(fs, s);
+    int ffail = 0, efail = 0;
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+      int fsv = 0, esv = 0;
+      for (int j = 0; j < k; ++j) {
+        const int e = c * k + j;
+        fsv ^= fsyn[(size_t)f * E + e];
+        esv ^= gf_mul(__ldg(edge_h + e), sym[(size_t)f * N + __ldg(edge_var + e)], gexp, glog);
+      }
+      ffail |= fsv != 0;
+      efail |= esv != 0;
+    }
+    ffail = __syncthreads_or(ffail);
+    efail = __syncthreads_or(efail);
+    if (threadIdx.x == 0) {
+      if (!ffail && !efail) {
+        ok[f] = 1;
+        iters[f] = iter;
+      } else if (iter >= max_iter) {
+        ok[f] = efail ? 0 : 1;
+        iters[f] = iter;
+      } else {
+        next_list[atomicAdd(next_count, 1)] = f;
+      }
+      if (ffail != efail) atomicAdd(stats, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+static int grid_for(long long work_blocks, int per_sm) {
+  const long long cap = (long long)sm_count() * per_sm;
+  long long g = work_blocks < cap ? work_blocks : cap;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+
+#define NBFD_DISPATCH_M(m, FN) \
+  switch (m) {                 \
+    case 2: FN(2); break;      \
+    case 3: FN(3); break;      \
+    case 4: FN(4); break;      \
+    case 5: FN(5); break;      \
+    case 6: FN(6); break;      \
+    case 7: FN(7); break;      \
+    case 8: FN(8); break;      \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lambda0, float *v2c,
+                        int32_t *list_out, int32_t *count_out, cudaStream_t s) {
+  const long long total = (long long)F * c->N;
+#define NBFD_INIT(MB)                                                                        \
+  {                                                                                          \
+    using CL = ChannelLayout<MB>;                                                            \
+    const int grid = grid_for((total + 8 * CL::VPW - 1) / (8 * CL::VPW), 8);                 \
+    k_init<MB><<<grid, 256, 0, s>>>(llr, lambda0, v2c, c->d_var_edges, c->N, c->E, F,        \
+                                    list_out, count_out);                                    \
+  }
+  NBFD_DISPATCH_M(c->m, NBFD_INIT)
+#undef NBFD_INIT
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
+                         cudaStream_t s) {
+  const int Fmax = fs.n_static;
+  const size_t smem = (size_t)256 * c->k * sizeof(float);
+#define NBFD_CHECK_K(MB, KM)                                                                 \
+  {                                                                                          \
+    constexpr int IPB = 256 / (1 << MB);                                                     \
+    const int grid = grid_for(((long long)Fmax * c->M + IPB - 1) / IPB, 8);                  \
+    if (smem > 48 * 1024)                                                                    \
+      cudaFuncSetAttribute(k_check<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                           (int)smem);                                                       \
+    k_check<MB, KM><<<grid, 256, smem, s>>>(v2c, c2v, c->d_edge_h, c->d_perm, c->M, c->k,    \
+                                            c->E, fs);                                       \
+  }
+#define NBFD_CHECK(MB)                    \
+  {                                       \
+    if (c->k <= 4) NBFD_CHECK_K(MB, 4)    \
+    else if (c->k <= 8) NBFD_CHECK_K(MB, 8)   \
+    else if (c->k <= 16) NBFD_CHECK_K(MB, 16) \
+    else NBFD_CHECK_K(MB, 32)             \
+  }
+  NBFD_DISPATCH_M(c->m, NBFD_CHECK)
+#undef NBFD_CHECK
+#undef NBFD_CHECK_K
+  return cudaGetLastError();
+}
+
+bool form_supported(int form, int m) {
+  (void)m;
+  return form == NBFD_FORM_FP32_DIRECT;
+}
+
+cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
+                       const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn,
+                       cudaStream_t s) {
+  if (!form_supported(form, c->m)) return cudaErrorNotSupported;
+  const long long total = (long long)fs.n_static * c->N;
+#define NBFD_VAR(MB)                                                                       \
+  {                                                                                        \
+    constexpr int Q = 1 << MB, R = Q < 8 ? Q : 8, VPW = 32 / (Q / R);                      \
+    const int grid = grid_for((total + 8 * VPW - 1) / (8 * VPW), 8);                       \
+    k_var_direct<MB><<<grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,        \
+                                          c->d_edge_h, c->d_perm, c->N, c->E, fs);         \
+  }
+  NBFD_DISPATCH_M(c->m, NBFD_VAR)
+#undef NBFD_VAR
+  return cudaGetLastError();
+}
+
+cudaError_t launch_syndrome(const nbfd_code *c, int F, const uint16_t *sym, const uint8_t *fsyn,
+                            uint16_t *fourier, uint16_t *exact, cudaStream_t s) {
+  const long long total = (long long)F * c->M;
+  const int grid = grid_for((total + 255) / 256, 8);
+  k_syndrome<<<grid, 256, 0, s>>>(sym, fsyn, fourier, exact, c->d_edge_var, c->d_edge_h,
+                                  c->d_gf_exp, c->d_gf_log, c->N, c->M, c->k, c->E, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, const uint8_t *fsyn,
+                        int iter, int max_iter, int32_t *next_list, int32_t *next_count,
+                        uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s) {
+  const int grid = grid_for(fs.n_static, 16);
+  k_stop<<<grid, 128, 0, s>>>(fs, sym, fsyn, c->d_edge_var, c->d_edge_h, c->d_gf_exp,
+                              c->d_gf_log, c->q, c->N, c->M, c->k, c->E, iter, max_iter,
+                              next_list, next_count, ok, iters, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace nbfd

@@ -1,0 +1,56 @@
+// Internal declarations shared by the translation units of libnbfd.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "nbfd.h"
+
+struct nbfd_code {
+  int N = 0, M = 0, k = 0, m = 0, q = 0, E = 0;
+  uint32_t poly = 0;
+  int device = 0;
+  std::vector<int32_t> caller_edge_of_slot;  // [E]
+  std::vector<uint8_t> index_map;            // [q][q]: H z for h = row (Appendix A)
+  // device tables, carved from one allocation
+  void *d_block = nullptr;
+  int32_t *d_edge_var = nullptr;   // [E] variable of each slot (check-major)
+  uint8_t *d_edge_h = nullptr;     // [E] h of each slot
+  int32_t *d_var_edges = nullptr;  // [N][2] the two slots of each variable
+  uint8_t *d_perm = nullptr;       // [q][q] index map, row h
+  uint8_t *d_gf_exp = nullptr;     // [2q] alpha^i, i in [0, 2q)
+  uint8_t *d_gf_log = nullptr;     // [q]  log_alpha(x), x != 0
+};
+
+namespace nbfd {
+
+// Frames a launch works on: either frames 0..n_static-1, or the first *count entries of list.
+struct FrameSet {
+  const int32_t *list = nullptr;
+  const int32_t *count = nullptr;
+  int n_static = 0;
+};
+
+int set_error(int status, const char *fmt, ...);
+int check_cuda(cudaError_t e, const char *what);
+int sm_count();
+
+// kernel launchers (return cudaGetLastError() after the launch)
+cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lambda0, float *v2c,
+                        int32_t *list_out, int32_t *count_out, cudaStream_t s);
+cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
+                         cudaStream_t s);
+cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
+                       const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s);
+cudaError_t launch_syndrome(const nbfd_code *c, int F, const uint16_t *sym, const uint8_t *fsyn,
+                            uint16_t *fourier, uint16_t *exact, cudaStream_t s);
+// Stop test + compaction of one decoding iteration (see decode.cu).
+cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, const uint8_t *fsyn,
+                        int iter, int max_iter, int32_t *next_list, int32_t *next_count,
+                        uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s);
+bool form_supported(int form, int m);
+
+}  // namespace nbfd
