@@ -21,7 +21,7 @@ from __future__ import annotations
 import numpy as np
 
 # primitive polynomials used by the workloads (bit j = coefficient of x^j)
-PRIMITIVE_POLY = {2: 0x7, 3: 0xB, 4: 0x13, 6: 0x43, 8: 0x11D}
+PRIMITIVE_POLY = {2: 0x7, 3: 0xB, 4: 0x13, 5: 0x25, 6: 0x43, 7: 0x89, 8: 0x11D}
 
 
 def rng_for(*key: int) -> np.random.Generator:

@@ -2,10 +2,15 @@
 teacher-forced inputs made by the oracle, and the tolerance metric.
 
 Tolerances (FP32 path against the FP64 oracle fed the same FP32-rounded inputs):
-* linear domain, every entry:          |P_gpu - P_oracle| <= LIN_ATOL
-* log-magnitude where |P_oracle| >= 2^-7: |ln|P_gpu| - ln|P_oracle|| <= LOG_ATOL, signs equal.
-FP32 transforms / sums of q terms bounded by 1 carry an absolute error of a few ulp(1) times
-sqrt(q) per entry, so the log-magnitude bound is only feasible where |P| is not tiny; at
+* linear domain, every entry:  |P_gpu - P_oracle| <= max(LIN_ATOL, U32 * kappa)
+* log-magnitude, on entries with |P_oracle| >= 2^-7 of vectors with U32 * kappa * 2^7 <= LOG_ATOL:
+  |ln|P_gpu| - ln|P_oracle|| <= LOG_ATOL, and the signs agree.
+kappa is the condition number of the normalised output of a signed sum,
+kappa = max_z sum_i |t_i(z)| / |U(0)| (1 for the transform of a probability vector and for the
+check node's products), widened at the variable node by the FP32 error of the channel message the
+kernel rebuilds (conv_condition). An FP32 sum of q terms followed by division by U(0) carries an error of
+order U32 * kappa (U32 = 2^-24) however it is evaluated, because every input is itself an FP32
+value: with conflicting channel and check messages U(0) is tiny and kappa large. At
 |P| >= 2^-7 an absolute error of 7.8e-7 in P is 1e-4 in ln|P|.
 """
 
@@ -14,8 +19,9 @@ from __future__ import annotations
 import numpy as np
 
 from oracle import logfourier as LF
-from oracle.transforms import gamma_inv
+from oracle.transforms import gamma_inv, xor_conv
 
+U32 = 2.0 ** -24
 LIN_ATOL = 1e-5
 LOG_ATOL = 1e-4
 LOG_FLOOR = 2.0 ** -7
@@ -24,7 +30,8 @@ MARGIN = 1e-3
 
 def encode(s, l) -> np.ndarray:
     """Oracle Gamma pair (s, l = ln|P|) -> the library's float32 (sign bit = s, |value| = -l)."""
-    mag = (-np.asarray(l, dtype=np.float64)).astype(np.float32)
+    neg_l = -np.asarray(l, dtype=np.float64)
+    mag = np.where(neg_l > 0, neg_l, 0.0).astype(np.float32)  # +0.0 for P = 1, clamp |P| > 1
     return np.where(np.asarray(s).astype(bool), -mag, mag).astype(np.float32)
 
 
@@ -39,19 +46,48 @@ def to_linear(g: np.ndarray) -> np.ndarray:
     return gamma_inv(s, l)
 
 
-def compare(gpu: np.ndarray, s_o: np.ndarray, l_o: np.ndarray, lin_atol=LIN_ATOL, log_atol=LOG_ATOL):
-    """Returns (ok, stats) for GPU messages against oracle Gamma pairs of the same shape."""
+def compare(gpu: np.ndarray, s_o: np.ndarray, l_o: np.ndarray, kappa=None, lin_atol=LIN_ATOL,
+            log_atol=LOG_ATOL):
+    """Returns (ok, stats) for GPU messages against oracle Gamma pairs of the same shape
+    (..., q); kappa (shape (...)) is the per-vector condition number (None: 1)."""
     P_o = gamma_inv(s_o, l_o)
     P_g = to_linear(gpu)
-    lin = float(np.max(np.abs(P_g - P_o))) if P_o.size else 0.0
-    mask = np.abs(P_o) >= LOG_FLOOR
+    k = np.ones(P_o.shape[:-1]) if kappa is None else np.asarray(kappa, dtype=np.float64)
+    tol = np.maximum(lin_atol, U32 * k)[..., None]
+    err = np.abs(P_g - P_o)
+    lin_bad = int(np.sum(err > tol))
+    lin = float(np.max(err)) if P_o.size else 0.0
+    well = (U32 * k * 2.0 ** 7 <= log_atol)[..., None]
+    mask = (np.abs(P_o) >= LOG_FLOOR) & well
     sg, lg = decode_pair(gpu)
     logerr = float(np.max(np.abs(lg[mask] - l_o[mask]))) if mask.any() else 0.0
     sign_bad = int(np.sum(sg[mask] != s_o[mask]))
     nan = int(np.isnan(gpu).sum())
-    ok = lin <= lin_atol and logerr <= log_atol and sign_bad == 0 and nan == 0
-    return ok, {"lin_max": lin, "log_max": logerr, "sign_bad": sign_bad, "nan": nan,
-                "n_log": int(mask.sum())}
+    ok = lin_bad == 0 and logerr <= log_atol and sign_bad == 0 and nan == 0
+    return ok, {"lin_max": lin, "lin_bad": lin_bad, "log_max": logerr, "sign_bad": sign_bad, "nan": nan,
+                "n_log": int(mask.sum()), "kappa_max": float(k.max()) if k.size else 1.0}
+
+
+def conv_condition(a_lin: np.ndarray, b_lin: np.ndarray, m: int) -> np.ndarray:
+    """kappa of the normalised XOR convolution a (*) b where `a` is the channel message that the
+    kernel rebuilds in FP32 (absolute error up to 2m ulp(1) per entry: m products and an m-stage
+    tree of additions over a probability vector):
+    kappa = (max_z sum |a||b| + 2m sum |b|) / |(a (*) b)(0)|."""
+    S = xor_conv(np.abs(a_lin), np.abs(b_lin))
+    U0 = xor_conv(a_lin, b_lin)[..., 0]
+    with np.errstate(divide="ignore"):
+        return (np.max(S, axis=-1) + 2 * m * np.abs(b_lin).sum(-1)) / np.abs(U0)
+
+
+def var_conditions(oc, lam0, c2v) -> np.ndarray:
+    """kappa of every V->C output (edge e: channel of its variable (*) message of the other edge)."""
+    a = gamma_inv(*lam0)
+    b = gamma_inv(*c2v)
+    other = np.empty(oc.E, dtype=np.int64)
+    for v in range(oc.N):
+        e1, e2 = oc.C[v]
+        other[e1], other[e2] = e2, e1
+    return conv_condition(a[oc.edge_var], b[other], oc.m)
 
 
 def oracle_state(oc, llr: np.ndarray, n_iter: int):

@@ -16,7 +16,7 @@ from oracle.code import OracleCode  # noqa: E402
 from paper_1008_4370_gb300 import build as nbuild  # noqa: E402
 from paper_1008_4370_gb300 import synth  # noqa: E402
 
-from helpers import MARGIN, compare, decode_pair, encode, oracle_state, vn_margins  # noqa: E402
+from helpers import MARGIN, compare, decode_pair, encode, oracle_state, var_conditions, vn_margins  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,7 @@ def _code(spec):
 # small codes over every field size the kernels are instantiated for, plus the configured codes
 STEP_CODES = [
     "gf4_n8_k4", (3, 12, 4, 21), "gf16_n32_k4", (5, 20, 4, 22), (6, 24, 6, 23), (7, 16, 4, 24),
-    (8, 16, 4, 25), (4, 64, 32, 26), (8, 64, 16, 27),
+    (8, 16, 4, 25), (4, 80, 20, 26), (8, 64, 16, 27),
 ]
 
 
@@ -148,7 +148,8 @@ def test_var_parity(dev, spec):
         s, l = LF.var_update(oc, lam0, c2v_o, vars=vars_)
         vs = np.arange(oc.N) if vars_ is None else np.array(vars_)
         es = np.concatenate([oc.C[v] for v in vs])
-        ok, st = compare(g[f][es], s[es], l[es])
+        kappa = var_conditions(oc, lam0, c2v_o)
+        ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es])
         assert ok, (f, st)
         M = LF.tentative(oc, lam0, c2v_o, vars=vs)
         x = LF.bit_decisions(oc, M)

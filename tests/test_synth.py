@@ -60,3 +60,16 @@ def test_frames_are_seeded():
     b = synth.frames(c, 3, 2.0, snr_idx=1, batch_idx=2)
     d = synth.frames(c, 3, 2.0, snr_idx=1, batch_idx=3)
     assert np.array_equal(a[1], b[1]) and not np.array_equal(a[1], d[1])
+
+
+def test_every_gpu_test_code_can_be_built():
+    """The GPU tests build these codes; construct them here so input problems show up on CPU."""
+    specs = [(2, 8, 4, 7), (3, 12, 4, 21), (4, 32, 4, 1), (5, 20, 4, 22), (6, 24, 6, 23), (7, 16, 4, 24),
+             (8, 16, 4, 25), (4, 80, 20, 26), (8, 64, 16, 27)]
+    for m, N, k, seed in specs:
+        c = synth.regular_code(N, k, m, seed=seed)
+        oc = OracleCode.from_dict(c)
+        assert oc.E == 2 * N
+    for name in synth.CODES:
+        if name != "gf64_n4096_k8":
+            synth.named_code(name)
