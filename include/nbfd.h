@@ -123,6 +123,34 @@ int nbfd_decode(const nbfd_code *code, int n_frames, const float *llr_dev, int m
                 uint16_t *symbols_dev, uint8_t *syndrome_ok_dev, int32_t *iters_dev,
                 void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
+/* ---- decoding without device allocation ----------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers of the library. */
+
+/* Size of the fixed scratch array behind nbfd_decode_noalloc (64 MiB). */
+#define NBFD_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/*
+ * nbfd_decode_noalloc -- the same decoding as nbfd_decode (same arguments, same outputs, same
+ * once-per-iteration synchronisation with `cuda_stream`), for callers that must not allocate
+ * device memory while decoding: a receiver whose device memory another runtime reserved up
+ * front, or a real-time loop where cudaMalloc/cudaFree are banned because they may synchronise
+ * the device and take unbounded time. It calls no allocating routine.
+ *   - Its scratch is a fixed NBFD_NOALLOC_SCRATCH_BYTES array inside the library, created when the
+ *     library's device code is loaded on a device and held on every such device until the
+ *     process exits.
+ *   - The first call on each device looks the array's address up (with that device current);
+ *     make that first call before any stream capture.
+ *   - A batch whose scratch (nbfd_decode_workspace_size) exceeds the array is rejected with
+ *     NBFD_ENOMEM and a message; split it into smaller calls. At GF(256), N = 512 and
+ *     max_iter <= 100 that is up to 31 frames per call.
+ *   - Every call uses the same array and clears what it needs at its start. Calls whose GPU work
+ *     can overlap (different streams without ordering between them, or several host threads)
+ *     race on the array and corrupt each other's results: order them.
+ */
+int nbfd_decode_noalloc(const nbfd_code *code, int n_frames, const float *llr_dev, int max_iter,
+                        int form, uint16_t *symbols_dev, uint8_t *syndrome_ok_dev,
+                        int32_t *iters_dev, void *cuda_stream);
+
 /* ---- step-level entry points (one step of Section 3.2 each, all frames, no early stop) -- */
 
 /*

@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "NbfdError", "lib", "FORM_FP32_DIRECT", "FORM_BF16_HGEMM", "FORM_FP16_HGEMM", "FORM_FP32_FWHT",
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
-    "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_init_messages",
+    "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode",
 ]
@@ -27,6 +27,7 @@ FORM_BF16_HGEMM = 1
 FORM_FP16_HGEMM = 2
 FORM_FP32_FWHT = 3
 KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME = 0, 1, 2, 3
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libnbfd.so")
 
@@ -42,6 +43,7 @@ SIGNATURES = [
     ("nbfd_field_index_map", _I, [_I, ctypes.c_uint32, _P]),
     ("nbfd_decode_workspace_size", ctypes.c_size_t, [_P, _I, _I, _I]),
     ("nbfd_decode", _I, [_P, _I, _P, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    ("nbfd_decode_noalloc", _I, [_P, _I, _P, _I, _I, _P, _P, _P, _P]),
     ("nbfd_init_messages", _I, [_P, _I, _P, _P, _P, _P]),
     ("nbfd_check_update", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_var_update", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
@@ -162,6 +164,15 @@ def nbfd_decode(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, ite
                              _dptr(symbols),
                              _dptr(syndrome_ok, torch.uint8), _dptr(iters, torch.int32),
                              _dptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def nbfd_decode_noalloc(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, iters, stream=None):
+    """nbfd_decode without any device allocation: scratch lives in a fixed array of
+    NOALLOC_SCRATCH_BYTES inside the library (see include/nbfd.h for who needs this)."""
+    import torch
+    _check(lib().nbfd_decode_noalloc(handle, int(n_frames), _dptr(llr, torch.float32), int(max_iter), int(form),
+                                     _dptr(symbols), _dptr(syndrome_ok, torch.uint8), _dptr(iters, torch.int32),
+                                     _stream(stream)))
 
 
 def nbfd_init_messages(handle, n_frames, llr, lambda0, v2c, stream=None):
