@@ -26,6 +26,7 @@ FORM_FP32_DIRECT = 0
 FORM_BF16_HGEMM = 1
 FORM_FP16_HGEMM = 2
 FORM_FP32_FWHT = 3
+SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT)
 KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME = 0, 1, 2, 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
 

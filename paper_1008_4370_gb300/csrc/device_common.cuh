@@ -35,12 +35,11 @@ struct ChannelLayout {
   static constexpr int LOG_VPT = MB - (Q >= 32 ? 5 : MB);
 };
 
-// P0(z) = sum_x p0(x) (-1)^{z.x} for one variable, p0(x) = prod_i Pr(b_i = x_i | L_i).
-// Lane l of a group of LPV lanes holds z = l*VPT + j in P[j]. All 32 lanes of the warp must
-// call this together (shuffles). `L` points at the MB LLRs of this lane's variable.
+// p0(x) = prod_i Pr(b_i = x_i | L_i) for one variable, at x = l*VPT + j in P[j] (lane l of a
+// group of LPV lanes). `L` points at the MB LLRs of this lane's variable.
 template <int MB>
-__device__ __forceinline__ void channel_fourier(const float *__restrict__ L, int l,
-                                                float (&P)[ChannelLayout<MB>::VPT]) {
+__device__ __forceinline__ void channel_probs(const float *__restrict__ L, int l,
+                                              float (&P)[ChannelLayout<MB>::VPT]) {
   using CL = ChannelLayout<MB>;
   float pb0[MB], pb1[MB];
 #pragma unroll
@@ -59,28 +58,43 @@ __device__ __forceinline__ void channel_fourier(const float *__restrict__ L, int
     for (int i = 0; i < MB; ++i) p *= ((x >> i) & 1) ? pb1[i] : pb0[i];
     P[j] = p;
   }
-  // butterflies on the bits held in registers
+}
+
+// In-place Walsh-Hadamard transform (Section 2.1, without the 1/2^m of the inverse) of one
+// length-Q vector spread over a group of LPV lanes, index l*VPT + j in V[j]: butterflies on the
+// index bits held in registers, then on the bits spread over lanes (warp shuffles). All 32 lanes
+// of the warp must call this together.
+template <int MB>
+__device__ __forceinline__ void wht_inplace(float (&V)[ChannelLayout<MB>::VPT], int l) {
+  using CL = ChannelLayout<MB>;
 #pragma unroll
   for (int b = 0; b < CL::LOG_VPT; ++b) {
 #pragma unroll
     for (int j = 0; j < CL::VPT; ++j) {
       if (!(j & (1 << b))) {
-        const float u = P[j], w = P[j | (1 << b)];
-        P[j] = u + w;
-        P[j | (1 << b)] = u - w;
+        const float u = V[j], w = V[j | (1 << b)];
+        V[j] = u + w;
+        V[j | (1 << b)] = u - w;
       }
     }
   }
-  // butterflies on the bits spread over lanes
 #pragma unroll
   for (int b = CL::LOG_VPT; b < MB; ++b) {
     const int lb = 1 << (b - CL::LOG_VPT);
 #pragma unroll
     for (int j = 0; j < CL::VPT; ++j) {
-      const float o = __shfl_xor_sync(kFull, P[j], lb);
-      P[j] = (l & lb) ? (o - P[j]) : (P[j] + o);
+      const float o = __shfl_xor_sync(kFull, V[j], lb);
+      V[j] = (l & lb) ? (o - V[j]) : (V[j] + o);
     }
   }
+}
+
+// P0(z) = sum_x p0(x) (-1)^{z.x} for one variable (INITIALIZATION of Section 3.2).
+template <int MB>
+__device__ __forceinline__ void channel_fourier(const float *__restrict__ L, int l,
+                                                float (&P)[ChannelLayout<MB>::VPT]) {
+  channel_probs<MB>(L, l, P);
+  wht_inplace<MB>(P, l);
 }
 
 }  // namespace nbfd

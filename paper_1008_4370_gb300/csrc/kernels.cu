@@ -475,13 +475,14 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
 
 bool form_supported(int form, int m) {
   (void)m;
-  return form == NBFD_FORM_FP32_DIRECT;
+  return form == NBFD_FORM_FP32_DIRECT || form == NBFD_FORM_FP32_FWHT;
 }
 
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn,
                        cudaStream_t s) {
   if (!form_supported(form, c->m)) return cudaErrorNotSupported;
+  if (form == NBFD_FORM_FP32_FWHT) return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, s);
   const long long total = (long long)fs.n_static * c->N;
 #define NBFD_VAR(MB)                                                                       \
   {                                                                                        \

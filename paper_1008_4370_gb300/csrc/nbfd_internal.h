@@ -52,5 +52,7 @@ cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, co
                         int iter, int max_iter, int32_t *next_list, int32_t *next_count,
                         uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s);
 bool form_supported(int form, int m);
+cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
+                            float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s);
 
 }  // namespace nbfd

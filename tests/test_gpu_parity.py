@@ -123,8 +123,12 @@ def test_check_parity(dev, spec):
         assert ok, (f, st)
 
 
+FORMS = [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT]
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("spec", STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6"])
-def test_var_parity(dev, spec):
+def test_var_parity(dev, spec, form):
     c = _code(spec)
     oc = OracleCode.from_dict(c)
     F = 2
@@ -137,7 +141,7 @@ def test_var_parity(dev, spec):
     v2c = torch.empty((F, oc.E, oc.q), dtype=torch.float32, device=dev)
     sym = torch.zeros((F, oc.N), dtype=torch.int16, device=dev)
     fsyn = torch.zeros((F, oc.E), dtype=torch.uint8, device=dev)
-    nb.nbfd_var_update(code.handle, F, nb.FORM_FP32_DIRECT, _t(llr, dev), _t(c2v_in, dev), v2c, sym, fsyn)
+    nb.nbfd_var_update(code.handle, F, form, _t(llr, dev), _t(c2v_in, dev), v2c, sym, fsyn)
     torch.cuda.synchronize()
     g, gs, gw = v2c.cpu().numpy(), sym.cpu().numpy().astype(np.int64), fsyn.cpu().numpy().astype(np.int64)
     vars_ = None if oc.N <= 64 else list(range(0, oc.N, max(1, oc.N // 40)))
@@ -186,7 +190,7 @@ def test_syndrome_parity(dev):
     assert not ex.cpu().numpy()[0].any()
 
 
-def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5):
+def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5, form=nb.FORM_FP32_DIRECT):
     """Whole decodes on both sides. Bit-exact symbols and syndrome flags are required on frames
     the oracle decodes (or runs to max_iter) whose last-iteration margin exceeds MARGIN; equal
     iteration counts on frames whose margin exceeds MARGIN at every iteration. Messages do not
@@ -194,7 +198,7 @@ def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5):
     oc = OracleCode.from_dict(c)
     code = nb.Code(c)
     F = llr.shape[0]
-    sym, ok, it = nb.decode(code, _t(llr, dev), max_iter, nb.FORM_FP32_DIRECT)
+    sym, ok, it = nb.decode(code, _t(llr, dev), max_iter, form)
     torch.cuda.synchronize()
     sym, ok, it = sym.cpu().numpy().astype(np.int64), ok.cpu().numpy(), it.cpu().numpy()
     n_sym = n_it = 0
@@ -212,19 +216,21 @@ def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5):
     return sym, ok, it, n_sym, n_it
 
 
-def test_decode_parity_tiny_gf16(dev):
+@pytest.mark.parametrize("form", FORMS)
+def test_decode_parity_tiny_gf16(dev, form):
     """Tiny configuration: GF(16) (2,4) N=32, all-zero codeword at Eb/N0 = 2 dB, 100 frames,
     at most 50 iterations."""
     c = synth.named_code("gf16_n32_k4")
     _, llr = synth.frames(c, 100, 2.0, zero_codeword=True)
-    sym, ok, it, n_sym, n_it = _decode_vs_oracle(dev, c, llr, 50, min_frac=0.6)
+    sym, ok, it, n_sym, n_it = _decode_vs_oracle(dev, c, llr, 50, min_frac=0.6, form=form)
     assert ok.mean() > 0.5 and it.min() >= 1 and it.max() <= 50
 
 
-def test_decode_parity_gf4_n8(dev):
+@pytest.mark.parametrize("form", FORMS)
+def test_decode_parity_gf4_n8(dev, form):
     c = synth.named_code("gf4_n8_k4")
     _, llr = synth.frames(c, 64, 1.0)
-    _decode_vs_oracle(dev, c, llr, 20, min_frac=0.6)
+    _decode_vs_oracle(dev, c, llr, 20, min_frac=0.6, form=form)
 
 
 def test_decode_edge_cases(dev):
@@ -259,15 +265,16 @@ def test_decode_edge_cases(dev):
     assert ei.value.status == -10
 
 
-def test_decode_full_size_gf256_n512(dev):
+@pytest.mark.parametrize("form", FORMS)
+def test_decode_full_size_gf256_n512(dev, form):
     """The measured configuration: GF(256) (2,4) N=512, 1024 frames at Eb/N0 = 1.5 dB. With at
     most 4 iterations two sampled frames are decoded by the oracle as well; with 100 iterations
     every frame is checked for properties that hold at any size."""
     c = synth.named_code("gf256_n512_k4")
     tx, llr = synth.frames(c, 1024, 1.5)
-    _decode_vs_oracle(dev, c, llr, 4, frames=[0, 777], min_frac=0.5)
+    _decode_vs_oracle(dev, c, llr, 4, frames=[0, 777], min_frac=0.5, form=form)
     code = nb.Code(c)
-    sym, ok, it = nb.decode(code, _t(llr, dev), 100, nb.FORM_FP32_DIRECT)
+    sym, ok, it = nb.decode(code, _t(llr, dev), 100, form)
     # self-consistency on every frame: the library's own syndrome of its output is 0 iff ok
     ex = torch.empty((1024, code.M), dtype=torch.int16, device=dev)
     nb.nbfd_syndrome(code.handle, 1024, sym, None, None, ex)
