@@ -198,7 +198,7 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       fs.count = w.count + it;
       fs.n_static = F;
       tm.begin(NBFD_KERNEL_CHECK, active, s);
-      if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s), "check kernel"))) break;
+      if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1), "check kernel"))) break;
       tm.end(s);
       tm.begin(NBFD_KERNEL_VAR, active, s);
       if ((st = check_cuda(launch_var(c, fs, form, llr, w.c2v, w.v2c, symbols, w.fsyn, s),
@@ -218,6 +218,16 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
       tm.flush();
       active = *host_count;
+    }
+    if (st == NBFD_OK) {
+      // stats[1] holds NBFD_ETIMEDOUT if a bounded device-side wait expired
+      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.stats + 1, sizeof(int32_t),
+                                           cudaMemcpyDeviceToHost, s),
+                           "cudaMemcpyAsync(status)")))
+        break;
+      if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
+      if (*host_count != 0)
+        st = set_error(NBFD_ETIMEDOUT, "a bounded device-side wait expired (status %d)", *host_count);
     }
   } while (false);
   tm.flush();

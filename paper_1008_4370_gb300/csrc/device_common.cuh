@@ -81,11 +81,61 @@ __device__ __forceinline__ void wht_inplace(float (&V)[ChannelLayout<MB>::VPT], 
 #pragma unroll
   for (int b = CL::LOG_VPT; b < MB; ++b) {
     const int lb = 1 << (b - CL::LOG_VPT);
+    const float sg = (l & lb) ? -1.0f : 1.0f;  // lower partner keeps V + o, upper o - V
 #pragma unroll
     for (int j = 0; j < CL::VPT; ++j) {
       const float o = __shfl_xor_sync(kFull, V[j], lb);
-      V[j] = (l & lb) ? (o - V[j]) : (V[j] + o);
+      V[j] = fmaf(sg, V[j], o);  // exact: a product with +-1 is not rounded
     }
+  }
+}
+
+// Gamma^{-1} with the fast exponential (ex2 unit); a few ulp of relative error per entry.
+__device__ __forceinline__ float gamma_decode_fast(float g) {
+  const float e = __expf(-fabsf(g));
+  return __uint_as_float(__float_as_uint(e) | (__float_as_uint(g) & 0x80000000u));
+}
+
+// Gamma(r) for |r| <= 1 with the fast logarithm (lg2 unit).
+__device__ __forceinline__ float gamma_encode_fast(float r) {
+  const float a = fabsf(r);
+  const float mag = a >= 1.0f ? 0.0f : -__logf(a);
+  const uint32_t s = (a > 0.0f) ? (__float_as_uint(r) & 0x80000000u) : 0u;
+  return __uint_as_float(__float_as_uint(mag) | s);
+}
+
+// channel_probs with the MB logistic pairs computed once per group (lane i < MB computes bit i,
+// then shuffles share them) and p(x) factored as p_low(j) * p_high(l) over the index bits held
+// in registers and across lanes. `L` points at the MB LLRs of this group's variable.
+template <int MB>
+__device__ __forceinline__ void channel_probs_shared(const float *__restrict__ L, int l,
+                                                     float (&P)[ChannelLayout<MB>::VPT]) {
+  using CL = ChannelLayout<MB>;
+  const int lane = threadIdx.x & 31;
+  const int base = lane - l;
+  float my0 = 1.0f, my1 = 0.0f;
+  if (l < MB) {
+    const float Li = __ldg(L + l);
+    const float e = expf(-fabsf(Li));
+    const float big = 1.0f / (1.0f + e), small = e / (1.0f + e);
+    my0 = Li >= 0.0f ? big : small;
+    my1 = Li >= 0.0f ? small : big;
+  }
+  float pb0[MB], pb1[MB];
+#pragma unroll
+  for (int i = 0; i < MB; ++i) {
+    pb0[i] = __shfl_sync(kFull, my0, base + i);
+    pb1[i] = __shfl_sync(kFull, my1, base + i);
+  }
+  float hi = 1.0f;
+#pragma unroll
+  for (int b = CL::LOG_VPT; b < MB; ++b) hi *= ((l >> (b - CL::LOG_VPT)) & 1) ? pb1[b] : pb0[b];
+#pragma unroll
+  for (int j = 0; j < CL::VPT; ++j) {
+    float p = hi;
+#pragma unroll
+    for (int b = 0; b < CL::LOG_VPT; ++b) p *= ((j >> b) & 1) ? pb1[b] : pb0[b];
+    P[j] = p;
   }
 }
 

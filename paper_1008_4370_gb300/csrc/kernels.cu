@@ -1,8 +1,7 @@
 // Kernels of one Log-Fourier decoding iteration (Section 3.2) on sm_103a.
 //
 //   k_init        INITIALIZATION: p0 from bit LLRs, transform with butterflies, Gamma form.
-//   k_check       CHECK TO VARIABLE: gather through H_cv, leave-one-out Gamma sums over the
-//                 other k-1 edges, scatter through H_cv^{-1}; staged in shared memory.
+//   (CHECK TO VARIABLE is the bulk-copy pipeline of kernels_check.cu.)
 //   k_var_direct  VARIABLE TO CHECK (boxplus of the channel message with the other check's
 //                 message, as q^2 signed products in FP32) + TENTATIVE DECISION (bits and
 //                 Fourier syndrome words from M_v at 3m points).
@@ -113,95 +112,6 @@ __global__ void __launch_bounds__(256)
         store_vec<VPT>(v2c + ((size_t)f * E + e2) * Q + l * VPT, g);
       }
     }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// CHECK TO VARIABLE
-// ---------------------------------------------------------------------------------------
-// 256 threads = IPB checks x Q entries. A check's k slots are contiguous ([slot][z]), so the
-// IPB checks are staged with 16-byte loads; thread (check i, z) gathers V->C entry H_e z of
-// every slot e, forms the leave-one-out sums with a prefix and a suffix pass (no subtraction,
-// so +inf magnitudes stay exact), and writes output z' = H_e z of slot e in place: for each
-// slot, z -> H_e z is a bijection, so every shared word is read and written by one thread only.
-template <int MB, int KMAX>
-__global__ void __launch_bounds__(256)
-    k_check(const float *__restrict__ v2c, float *__restrict__ c2v,
-            const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
-            int E, FrameSet fs) {
-  constexpr int Q = 1 << MB;
-  constexpr int IPB = 256 / Q;
-  extern __shared__ float4 sm4[];
-  float *sm = reinterpret_cast<float *>(sm4);
-  const long long total = (long long)frame_count(fs) * M;
-  const int it = threadIdx.x / Q, z = threadIdx.x % Q;
-  const int kq4 = k * Q / 4;
-  for (long long base = (long long)blockIdx.x * IPB; base < total;
-       base += (long long)gridDim.x * IPB) {
-    for (int idx = threadIdx.x; idx < IPB * kq4; idx += blockDim.x) {
-      const int i = idx / kq4, r = idx - i * kq4;
-      const long long item = base + i;
-      if (item < total) {
-        const long long slot = item / M;
-        const int c = static_cast<int>(item - slot * M);
-        const int f = frame_at(fs, slot);
-        const float4 *src =
-            reinterpret_cast<const float4 *>(v2c + ((size_t)f * E + (size_t)c * k) * Q);
-        sm4[idx] = __ldg(src + r);
-      }
-    }
-    __syncthreads();
-    const long long item = base + it;
-    if (item < total) {
-      const int c = static_cast<int>(item % M);
-      float *s = sm + (size_t)it * k * Q;
-      float mag[KMAX];
-      uint32_t sg[KMAX];
-      int pos[KMAX];
-      uint32_t sx = 0;
-#pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        if (e < k) {
-          const int h = __ldg(edge_h + (size_t)c * k + e);
-          pos[e] = __ldg(perm + h * Q + z);
-          const float x = s[e * Q + pos[e]];
-          mag[e] = fabsf(x);
-          sg[e] = __float_as_uint(x) & 0x80000000u;
-          sx ^= sg[e];
-        }
-      }
-      float suf[KMAX];
-      float run = 0.0f;
-#pragma unroll
-      for (int e = KMAX - 1; e >= 0; --e) {
-        if (e < k) {
-          suf[e] = run;
-          run += mag[e];
-        }
-      }
-      float pre = 0.0f;
-#pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        if (e < k) {
-          const float o = pre + suf[e];
-          pre += mag[e];
-          s[e * Q + pos[e]] = __uint_as_float(__float_as_uint(o) | (sx ^ sg[e]));
-        }
-      }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < IPB * kq4; idx += blockDim.x) {
-      const int i = idx / kq4, r = idx - i * kq4;
-      const long long item = base + i;
-      if (item < total) {
-        const long long slot = item / M;
-        const int c = static_cast<int>(item - slot * M);
-        const int f = frame_at(fs, slot);
-        float4 *dst = reinterpret_cast<float4 *>(c2v + ((size_t)f * E + (size_t)c * k) * Q);
-        dst[r] = sm4[idx];
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -447,30 +357,8 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
 }
 
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                         cudaStream_t s) {
-  const int Fmax = fs.n_static;
-  const size_t smem = (size_t)256 * c->k * sizeof(float);
-#define NBFD_CHECK_K(MB, KM)                                                                 \
-  {                                                                                          \
-    constexpr int IPB = 256 / (1 << MB);                                                     \
-    const int grid = grid_for(((long long)Fmax * c->M + IPB - 1) / IPB, 8);                  \
-    if (smem > 48 * 1024)                                                                    \
-      cudaFuncSetAttribute(k_check<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                           (int)smem);                                                       \
-    k_check<MB, KM><<<grid, 256, smem, s>>>(v2c, c2v, c->d_edge_h, c->d_perm, c->M, c->k,    \
-                                            c->E, fs);                                       \
-  }
-#define NBFD_CHECK(MB)                    \
-  {                                       \
-    if (c->k <= 4) NBFD_CHECK_K(MB, 4)    \
-    else if (c->k <= 8) NBFD_CHECK_K(MB, 8)   \
-    else if (c->k <= 16) NBFD_CHECK_K(MB, 16) \
-    else NBFD_CHECK_K(MB, 32)             \
-  }
-  NBFD_DISPATCH_M(c->m, NBFD_CHECK)
-#undef NBFD_CHECK
-#undef NBFD_CHECK_K
-  return cudaGetLastError();
+                         cudaStream_t s, int32_t *err) {
+  return launch_check_bulk(c, fs, v2c, c2v, err, s);
 }
 
 bool form_supported(int form, int m) {

@@ -1,0 +1,291 @@
+// CHECK TO VARIABLE (Section 3.2) as a bulk-copy pipeline.
+//
+// A check's k slots are one contiguous block of k*q floats ([slot][z], slots check-major), and
+// consecutive checks of a frame are contiguous too. A block owns a sequence of stages of T
+// checks; thread 0 streams the next S-1 stages into shared memory with cp.async.bulk (the bulk
+// copy engine, completion counted on one mbarrier per stage) while all 256 threads work on the
+// current stage in place: thread (i, z) gathers entry H_e z of every slot e of its check, forms
+// the leave-one-out Gamma sums (prefix and suffix passes: no subtraction, so +inf magnitudes
+// stay exact; signs XOR), and writes output H_e z of slot e back to the same word (z -> H_e z
+// is a bijection, so each word has one reader and one writer). Thread 0 then writes the stage
+// back with one bulk shared->global copy per run of checks of one frame.
+//
+// Every mbarrier wait is bounded by a clock budget: on expiry the kernel records
+// NBFD_ETIMEDOUT in *err, waits (bounded) for its own stores and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "nbfd_internal.h"
+
+namespace nbfd {
+
+namespace {
+
+constexpr long long kWaitBudgetCycles = 4000000000LL;  // ~2 s at the maximum SM clock
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitBudgetCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst_smem)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src_smem)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ int n_frames_of(const FrameSet &fs) {
+  return fs.list ? __ldg(fs.count) : fs.n_static;
+}
+__device__ __forceinline__ int frame_id(const FrameSet &fs, long long slot) {
+  return fs.list ? __ldg(fs.list + slot) : static_cast<int>(slot);
+}
+
+// Issue one bulk copy per run of consecutive checks of one frame in stage `st` (items
+// st*T .. st*T+T-1 of the flattened (frame slot, check) list). Returns the bytes moved.
+template <bool kLoad>
+__device__ uint32_t stage_copies(const FrameSet &fs, long long st, int T, long long total, int M,
+                                 int k, int E, int Q, const float *gsrc, float *gdst, float *sbuf,
+                                 uint64_t *bar) {
+  const uint32_t check_bytes = static_cast<uint32_t>(k * Q) * 4u;
+  uint32_t bytes = 0;
+  long long item = st * T;
+  const long long end = (st * T + T < total) ? st * T + T : total;
+  while (item < end) {
+    const long long slot = item / M;
+    const int c0 = static_cast<int>(item - slot * M);
+    long long run = M - c0;
+    if (item + run > end) run = end - item;
+    const int f = frame_id(fs, slot);
+    const size_t goff = ((size_t)f * E + (size_t)c0 * k) * Q;
+    float *s = sbuf + (size_t)(item - st * T) * k * Q;
+    const uint32_t nb = static_cast<uint32_t>(run) * check_bytes;
+    if constexpr (kLoad) {
+      bulk_load(s, gsrc + goff, nb, bar);
+    } else {
+      bulk_store(gdst + goff, s, nb);
+    }
+    bytes += nb;
+    item += run;
+  }
+  return bytes;
+}
+
+}  // namespace
+
+template <int MB, int KMAX>
+__global__ void __launch_bounds__(256)
+    k_check_bulk(const float *__restrict__ v2c, float *__restrict__ c2v,
+                 const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
+                 int E, int T, int S, FrameSet fs, int32_t *err) {
+  constexpr int Q = 1 << MB;
+  constexpr int IPB = 256 / Q;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  float *stages = reinterpret_cast<float *>(smem_raw + 128);
+  const size_t stage_floats = (size_t)T * k * Q;
+  const long long total = (long long)n_frames_of(fs) * M;
+  const long long n_stages = (total + T - 1) / T;
+  const long long my_first = blockIdx.x;
+  const long long my_count =
+      my_first < n_stages ? (n_stages - my_first + gridDim.x - 1) / gridDim.x : 0;
+  if (my_count == 0) return;
+  const int it = threadIdx.x / Q, z = threadIdx.x % Q;
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < S; ++b) mbar_init(&bars[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  long long issued = 0;  // stages whose loads thread 0 has issued (meaningful in thread 0)
+  if (threadIdx.x == 0) {
+    for (; issued < S - 1 && issued < my_count; ++issued) {
+      const long long st = my_first + issued * gridDim.x;
+      const int bi = static_cast<int>(issued % S);
+      const long long first = st * T;
+      const long long n = (first + T < total ? T : total - first);
+      mbar_expect_tx(&bars[bi], static_cast<uint32_t>(n) * k * Q * 4u);
+      stage_copies<true>(fs, st, T, total, M, k, E, Q, v2c, nullptr,
+                         stages + (size_t)bi * stage_floats, &bars[bi]);
+    }
+  }
+  long long i = 0;
+  bool failed = false;
+  for (; i < my_count; ++i) {
+    const int b = static_cast<int>(i % S);
+    const long long st = my_first + i * gridDim.x;
+    // prefetch stage i+S-1 into the buffer stage i-1 used, once its store has read it
+    if (threadIdx.x == 0 && issued < my_count) {
+      const long long stj = my_first + issued * gridDim.x;
+      const int bj = static_cast<int>(issued % S);
+      bulk_wait_read_all();
+      const long long first = stj * T;
+      const long long n = (first + T < total ? T : total - first);
+      mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n) * k * Q * 4u);
+      stage_copies<true>(fs, stj, T, total, M, k, E, Q, v2c, nullptr,
+                         stages + (size_t)bj * stage_floats, &bars[bj]);
+      ++issued;
+    }
+    const bool ok = mbar_wait_bounded(&bars[b], static_cast<uint32_t>((i / S) & 1));
+    if (__syncthreads_or(!ok)) {  // one verdict for the whole block
+      failed = true;
+      break;
+    }
+    float *sbuf = stages + (size_t)b * stage_floats;
+    const long long first = st * T;
+    for (int ci = it; ci < T; ci += IPB) {
+      const long long item = first + ci;
+      if (item >= total) break;
+      const int c = static_cast<int>(item % M);
+      float *s = sbuf + (size_t)ci * k * Q;
+      float mag[KMAX];
+      uint32_t sg[KMAX];
+      int pos[KMAX];
+      uint32_t sx = 0;
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) {
+        if (e < k) {
+          const int h = __ldg(edge_h + (size_t)c * k + e);
+          pos[e] = __ldg(perm + h * Q + z);
+          const float x = s[e * Q + pos[e]];
+          mag[e] = fabsf(x);
+          sg[e] = __float_as_uint(x) & 0x80000000u;
+          sx ^= sg[e];
+        }
+      }
+      float suf[KMAX];
+      float run = 0.0f;
+#pragma unroll
+      for (int e = KMAX - 1; e >= 0; --e) {
+        if (e < k) {
+          suf[e] = run;
+          run += mag[e];
+        }
+      }
+      float pre = 0.0f;
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) {
+        if (e < k) {
+          const float o = pre + suf[e];
+          pre += mag[e];
+          s[e * Q + pos[e]] = __uint_as_float(__float_as_uint(o) | (sx ^ sg[e]));
+        }
+      }
+    }
+    fence_proxy_async_smem();  // make the in-place results visible to the bulk copy engine
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      stage_copies<false>(fs, st, T, total, M, k, E, Q, nullptr, c2v, sbuf, nullptr);
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (failed) {
+      if (err) atomicExch(err, NBFD_ETIMEDOUT);
+      // loads still in flight land in this block's shared memory: wait for them (bounded)
+      for (long long j = i; j < issued; ++j)
+        mbar_wait_bounded(&bars[j % S], static_cast<uint32_t>((j / S) & 1));
+    }
+    bulk_wait_all();
+  }
+}
+
+cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
+                              int32_t *err, cudaStream_t s) {
+  const int Q = c->q, k = c->k;
+  const int ipb = 256 / Q;
+  // about 16 KiB of checks per stage, a multiple of the 256/Q checks one pass of threads covers
+  int g = (16 * 1024) / (ipb * k * Q * 4);
+  if (g < 1) g = 1;
+  const int T = ipb * g;
+  const int S = (size_t)T * k * Q * 4 > 24 * 1024 ? 3 : 4;
+  const size_t smem = 128 + (size_t)S * T * k * Q * 4;
+  const long long total = (long long)fs.n_static * c->M;
+  const long long n_stages = (total + T - 1) / T;
+  long long grid = (long long)sm_count() * (smem <= 56 * 1024 ? 3 : 2);
+  if (grid > n_stages) grid = n_stages;
+  if (grid < 1) grid = 1;
+#define NBFD_CHK(MB, KM)                                                                      \
+  {                                                                                           \
+    cudaFuncSetAttribute(k_check_bulk<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                         (int)smem);                                                          \
+    k_check_bulk<MB, KM><<<(int)grid, 256, smem, s>>>(v2c, c2v, c->d_edge_h, c->d_perm, c->M,  \
+                                                       k, c->E, T, S, fs, err);               \
+  }
+#define NBFD_CHK_M(MB)                     \
+  {                                        \
+    if (k <= 4) NBFD_CHK(MB, 4)            \
+    else if (k <= 8) NBFD_CHK(MB, 8)       \
+    else if (k <= 16) NBFD_CHK(MB, 16)     \
+    else NBFD_CHK(MB, 32)                  \
+  }
+  switch (c->m) {
+    case 2: NBFD_CHK_M(2) break;
+    case 3: NBFD_CHK_M(3) break;
+    case 4: NBFD_CHK_M(4) break;
+    case 5: NBFD_CHK_M(5) break;
+    case 6: NBFD_CHK_M(6) break;
+    case 7: NBFD_CHK_M(7) break;
+    case 8: NBFD_CHK_M(8) break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef NBFD_CHK_M
+#undef NBFD_CHK
+  return cudaGetLastError();
+}
+
+}  // namespace nbfd

@@ -92,13 +92,13 @@ __global__ void __launch_bounds__(256, 3)
     ld_global<VPT>(c2, c2v + ((size_t)f * E + e2) * Q + l * VPT);
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
-      c1[j] = gamma_decode(c1[j]);
-      c2[j] = gamma_decode(c2[j]);
+      c1[j] = gamma_decode_fast(c1[j]);
+      c2[j] = gamma_decode_fast(c2[j]);
     }
     wht_inplace<MB>(c1, l);  // q * (x-domain check message of e1)
     wht_inplace<MB>(c2, l);
     float p[VPT];
-    channel_probs<MB>(llr + ((size_t)f * N + v) * MB, l, p);  // x-domain channel message
+    channel_probs_shared<MB>(llr + ((size_t)f * N + v) * MB, l, p);  // x-domain channel message
     // M_v = p0 . c1x . c2x (all checks), read out below from shared memory
     float *m_sh = sM[wib] + sub * Q;
     float nm;
@@ -115,37 +115,46 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
     for (int j = 0; j < VPT; ++j) c2[j] *= p[j];
     wht_inplace<MB>(c2, l);
-    const float n1 = __shfl_sync(kFull, c2[0], sub * LPV);
+    const float r1 = 1.0f / __shfl_sync(kFull, c2[0], sub * LPV);
     if (valid) {
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) c2[j] = gamma_encode(c2[j] / n1);
+      for (int j = 0; j < VPT; ++j) c2[j] = gamma_encode_fast(c2[j] * r1);
       st_global<VPT>(v2c + ((size_t)f * E + e1) * Q + l * VPT, c2);
     }
 #pragma unroll
     for (int j = 0; j < VPT; ++j) c1[j] *= p[j];
     wht_inplace<MB>(c1, l);
-    const float n2 = __shfl_sync(kFull, c1[0], sub * LPV);
+    const float r2 = 1.0f / __shfl_sync(kFull, c1[0], sub * LPV);
     if (valid) {
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) c1[j] = gamma_encode(c1[j] / n2);
+      for (int j = 0; j < VPT; ++j) c1[j] = gamma_encode_fast(c1[j] * r2);
       st_global<VPT>(v2c + ((size_t)f * E + e2) * Q + l * VPT, c1);
     }
-    // TENTATIVE: signs of M at alpha^{i-1}, H_e1 alpha^{i-1}, H_e2 alpha^{i-1}
+    // TENTATIVE: signs of M at alpha^{i-1} (t < MB), H_e1 alpha^{i-1} (t < 2MB) and
+    // H_e2 alpha^{i-1} (t < 3MB), one read-out point per lane, gathered with ballots.
     __syncwarp();
-    if (valid && l == 0) {
-      const int h1 = __ldg(edge_h + e1), h2 = __ldg(edge_h + e2);
-      const uint32_t neg = nm < 0.0f ? 1u : 0u;
-      uint32_t bits = 0, w1 = 0, w2 = 0;
+    const int h1 = __ldg(edge_h + e1), h2 = __ldg(edge_h + e2);
+    uint32_t word = 0;
 #pragma unroll
-      for (int i = 0; i < MB; ++i) {
-        bits |= ((m_sh[1 << i] < 0.0f ? 1u : 0u) ^ neg) << i;
-        w1 |= ((m_sh[__ldg(perm + h1 * Q + (1 << i))] < 0.0f ? 1u : 0u) ^ neg) << i;
-        w2 |= ((m_sh[__ldg(perm + h2 * Q + (1 << i))] < 0.0f ? 1u : 0u) ^ neg) << i;
+    for (int r = 0; r < (3 * MB + LPV - 1) / LPV; ++r) {
+      const int t = r * LPV + l;
+      bool neg_pt = false;
+      if (t < 3 * MB) {
+        const int kind = t / MB, i = t - kind * MB;
+        const int z = kind == 0 ? (1 << i) : __ldg(perm + (kind == 1 ? h1 : h2) * Q + (1 << i));
+        neg_pt = m_sh[z] < 0.0f;
       }
-      if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(bits);
+      const uint32_t bal = __ballot_sync(kFull, neg_pt);
+      const uint32_t mine = LPV == 32 ? bal : (bal >> (sub * LPV)) & ((1u << LPV) - 1u);
+      word |= mine << (r * LPV);
+    }
+    if (nm < 0.0f) word = ~word;
+    if (valid && l == 0) {
+      const uint32_t mask = (1u << MB) - 1u;
+      if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(word & mask);
       if (fsyn) {
-        fsyn[(size_t)f * E + e1] = static_cast<uint8_t>(w1);
-        fsyn[(size_t)f * E + e2] = static_cast<uint8_t>(w2);
+        fsyn[(size_t)f * E + e1] = static_cast<uint8_t>((word >> MB) & mask);
+        fsyn[(size_t)f * E + e2] = static_cast<uint8_t>((word >> (2 * MB)) & mask);
       }
     }
     __syncwarp();

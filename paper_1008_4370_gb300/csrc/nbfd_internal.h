@@ -41,8 +41,11 @@ int sm_count();
 // kernel launchers (return cudaGetLastError() after the launch)
 cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lambda0, float *v2c,
                         int32_t *list_out, int32_t *count_out, cudaStream_t s);
+// err (device word, may be NULL) receives NBFD_ETIMEDOUT if a bounded wait of the kernel expired.
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                         cudaStream_t s);
+                         cudaStream_t s, int32_t *err = nullptr);
+cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
+                              int32_t *err, cudaStream_t s);
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s);
 cudaError_t launch_syndrome(const nbfd_code *c, int F, const uint16_t *sym, const uint8_t *fsyn,
