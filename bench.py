@@ -35,7 +35,7 @@ from paper_1008_4370_gb300 import synth  # noqa: E402
 
 CODE_NAME = "gf256_n512_k4"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
-FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3}
+FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 
 
 def parse():
@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="direct", choices=sorted(FORMS))
+    ap.add_argument("--form", default="fwht", choices=sorted(FORMS))
+    ap.add_argument("--plain-steps", type=int, default=3, help="steps of the plain FP32 direct form")
     ap.add_argument("--frames", type=int, default=1024)
     ap.add_argument("--ebn0", type=float, default=1.5)
     ap.add_argument("--max-iter", type=int, default=100)
@@ -144,6 +145,19 @@ class Clocks:
 
 # ---- the arms ---------------------------------------------------------------------------------
 
+def aggregate(local_seconds: float, local_frames: int, info_bits: int, dist=None, device=None):
+    """Whole-job throughput: frames of all ranks / the slowest rank's time (max over ranks)."""
+    import torch
+
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+    n = torch.tensor([float(local_frames)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    t_max, frames = float(t.item()), float(n.item())
+    return t_max, frames * info_bits / t_max / 1e6
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -161,6 +175,10 @@ def run_reference(a):
     cores = os.cpu_count() or 1
     _, llr = synth.frames(code, cores, a.ebn0, snr_idx=0, batch_idx=900)
     it_mean = reference_mean_iterations()
+    if it_mean is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle/workload_iterations.json is missing "
+                          "(run python -m oracle.measure_iterations)"}), flush=True)
+        return
     times = []
     fi = 0
     for s in range(a.warmup + a.steps):
@@ -185,12 +203,12 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def reference_mean_iterations() -> float:
+def reference_mean_iterations():
     p = os.path.join(ROOT, "oracle", "workload_iterations.json")
     if os.path.exists(p):
         with open(p) as f:
             return float(json.load(f)["mean_iterations"])
-    return 5.0
+    return None
 
 
 def run_ours(a):
@@ -262,10 +280,7 @@ def run_ours(a):
     nb.nbfd_prof_enable(False)
     clk = clocks.stop() if clocks else None
     dev_s = sum(step_ms) / 1e3
-    t_local = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local.item())
+    t_max, value = aggregate(dev_s, F * a.steps, info_bits, dist if world > 1 else None, dev)
 
     # decoding statistics of every batch (outside the timed region)
     fails, iters_all = 0, []
@@ -297,16 +312,29 @@ def run_ours(a):
         hit.copy_(its, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
-    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    _, e2e_value = aggregate(e2e_s, F * e2e_steps, info_bits, dist if world > 1 else None, dev)
+
+    # the plain FP32 direct form on the same batches (the "plain" side of served vs plain)
+    plain = None
+    if a.plain_steps > 0 and form != FORMS["direct"]:
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.plain_steps)]
+        nb.nbfd_decode(code.handle, F, batches[0][1], a.max_iter, FORMS["direct"], sym, ok, its, ws, need, stream)
+        torch.cuda.synchronize()
+        for i in range(a.plain_steps):
+            pe[i][0].record(stream)
+            nb.nbfd_decode(code.handle, F, batches[i % len(batches)][1], a.max_iter, FORMS["direct"], sym, ok,
+                           its, ws, need, stream)
+            pe[i][1].record(stream)
+        torch.cuda.synchronize()
+        p_s = sum(x.elapsed_time(y) for x, y in pe) / 1e3
+        p_t, p_value = aggregate(p_s, F * a.plain_steps, info_bits, dist if world > 1 else None, dev)
+        plain = {"form": "direct", "value": p_value, "unit": "Mbit/s", "steps": a.plain_steps,
+                 "ms_per_step": 1e3 * p_t / a.plain_steps}
     if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
         dist.destroy_process_group()
     if rank != 0:
         return
-
-    frames_total = F * a.steps * world
-    value = frames_total * info_bits / t_max / 1e6
-    e2e_value = F * e2e_steps * world * info_bits / float(t_e2e.item()) / 1e6
 
     # roofline of the dominant kernel
     peaks, peak_kind = load_peaks()
@@ -340,11 +368,14 @@ def run_ours(a):
         cores = os.cpu_count() or 1
         sample = batches[0][1][:cores].cpu().numpy()
         wall_c, fi = oracle_frame_iterations(sample, 2, cores)
-        cpu_val = info_bits * (fi / wall_c) / mean_iters / 1e6
+        it_ref, it_src = reference_mean_iterations(), "the oracle's own mean (oracle/workload_iterations.json)"
+        if it_ref is None:
+            it_ref, it_src = mean_iters, "the GPU run's mean"
+        cpu_val = info_bits * (fi / wall_c) / it_ref / 1e6
         cpu = {"value": cpu_val, "unit": "Mbit/s", "cores": cores, "kind": "oracle",
-               "sample": f"{cores} frames of the workload x up to 2 iterations, {cores} processes, "
-                         f"{fi} frame-iterations in {wall_c:.1f} s; converted at the GPU run's "
-                         f"{mean_iters:.2f} mean iterations per frame"}
+               "sample": f"{cores} frames of the workload x up to 2 iterations on {cores} processes: "
+                         f"{fi} frame-iterations in {wall_c:.1f} s, converted at {it_ref:.2f} "
+                         f"iterations per frame ({it_src})"}
 
     line = {
         "metric": "decoded Mbit/s (GF(256) (2,4) N=512)", "value": value, "unit": "Mbit/s",
@@ -361,6 +392,7 @@ def run_ours(a):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": F * N * m * 4,
                 "d2h_bytes_per_step": F * N * 2 + F + F * 4},
+        "plain_fp32": plain,
         "gpu_launches": launches_total,
         "roofline": roof,
         "clocks": clk,

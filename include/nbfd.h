@@ -50,6 +50,9 @@ extern "C" {
 #define NBFD_FORM_BF16_HGEMM 1  /* Hadamard transforms on tensor cores, BF16 in / FP32 acc */
 #define NBFD_FORM_FP16_HGEMM 2  /* same, FP16 in / FP32 acc */
 #define NBFD_FORM_FP32_FWHT 3   /* fast Walsh-Hadamard butterflies, FP32 */
+#define NBFD_FORM_FP32_TC 4     /* Hadamard transforms on tensor cores, operands split into three
+                                   bf16 parts (24 bits) with FP32 accumulate */
+/* The tensor-core forms (1, 2, 4) need m = 8 (q = 256 = 16 x 16); other m give NBFD_ENOTSUP. */
 
 typedef struct nbfd_code nbfd_code; /* opaque, library-owned, immutable after creation */
 

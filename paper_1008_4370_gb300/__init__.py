@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "NbfdError", "lib", "FORM_FP32_DIRECT", "FORM_BF16_HGEMM", "FORM_FP16_HGEMM", "FORM_FP32_FWHT",
+    "NbfdError", "lib", "FORM_FP32_DIRECT", "FORM_BF16_HGEMM", "FORM_FP16_HGEMM", "FORM_FP32_FWHT", "FORM_FP32_TC",
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
@@ -26,7 +26,9 @@ FORM_FP32_DIRECT = 0
 FORM_BF16_HGEMM = 1
 FORM_FP16_HGEMM = 2
 FORM_FP32_FWHT = 3
-SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT)
+FORM_FP32_TC = 4
+SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT, FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)
+TC_FORMS = (FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)  # need m = 8
 KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME = 0, 1, 2, 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
 

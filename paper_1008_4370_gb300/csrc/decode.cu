@@ -25,20 +25,28 @@ ProfTotals g_prof;
 
 struct PendingTimer {
   int kernel;
-  long long units;
+  int iter;  // decoding iteration of the launch (0 = INITIALIZATION)
   cudaEvent_t a, b;
 };
+
+// CUDA events around every launch; the frames each launch processed are taken from the
+// per-iteration active-frame counts once the decode is over.
+std::vector<cudaEvent_t> g_event_pool;  // reused across decodes (guarded by g_prof_mu)
 
 class Timers {
  public:
   explicit Timers(bool on) : on_(on) {}
   ~Timers() {
-    flush();
-    for (auto &e : pool_) cudaEventDestroy(e);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : pending_) {
+      g_event_pool.push_back(p.a);
+      g_event_pool.push_back(p.b);
+    }
   }
-  void begin(int kernel, long long units, cudaStream_t s) {
+  bool on() const { return on_; }
+  void begin(int kernel, int iter, cudaStream_t s) {
     if (!on_) return;
-    cur_ = {kernel, units, get(), get()};
+    cur_ = {kernel, iter, get(), get()};
     cudaEventRecord(cur_.a, s);
   }
   void end(cudaStream_t s) {
@@ -46,38 +54,42 @@ class Timers {
     cudaEventRecord(cur_.b, s);
     pending_.push_back(cur_);
   }
-  // Accumulate completed timers (the caller has synchronised the stream).
-  void flush() {
-    if (!on_ || pending_.empty()) return;
+  // counts[i] = frames active in iteration i (counts[0] unused: INITIALIZATION covers F frames).
+  void flush(const std::vector<int32_t> &counts, int F) {
+    if (!on_) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto &p : pending_) {
       float ms = 0.0f;
-      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      if (cudaEventSynchronize(p.b) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
         g_prof.ms[p.kernel] += ms;
         g_prof.launches[p.kernel] += 1;
-        g_prof.units[p.kernel] += p.units;
+        g_prof.units[p.kernel] +=
+            p.iter == 0 ? F : (p.iter < (int)counts.size() ? counts[p.iter] : 0);
       }
-      pool_.push_back(p.a);
-      pool_.push_back(p.b);
+      g_event_pool.push_back(p.a);
+      g_event_pool.push_back(p.b);
     }
     pending_.clear();
   }
 
  private:
-  cudaEvent_t get() {
-    if (!pool_.empty()) {
-      cudaEvent_t e = pool_.back();
-      pool_.pop_back();
-      return e;
+  static cudaEvent_t get() {
+    {
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+      }
     }
-    cudaEvent_t e;
+    cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
     return e;
   }
   bool on_;
   PendingTimer cur_{};
   std::vector<PendingTimer> pending_;
-  std::vector<cudaEvent_t> pool_;
 };
 
 // ---- workspace layout ----------------------------------------------------------------------
@@ -186,37 +198,48 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
     if ((st = check_cuda(cudaMemsetAsync(w.stats, 0, 64, s), "cudaMemsetAsync"))) break;
     if ((st = check_cuda(cudaMemsetAsync(ok, 0, (size_t)F, s), "cudaMemsetAsync"))) break;
     // INITIALIZATION (+ list of iteration 1 = all frames, count[1] = F)
-    tm.begin(NBFD_KERNEL_INIT, F, s);
+    tm.begin(NBFD_KERNEL_INIT, 0, s);
     if ((st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s),
                          "init kernel")))
       break;
     tm.end(s);
+    // The host reads the active-frame count every kSyncEvery iterations; in between it queues
+    // iterations blindly (a launch with no active frame returns at once) and sizes each grid by
+    // the last count it read, an upper bound since counts only shrink.
+    constexpr int kSyncEvery = 4;
     long long active = F;
-    for (int it = 1; it <= max_iter && active > 0; ++it) {
-      FrameSet fs;
-      fs.list = w.list[it & 1];
-      fs.count = w.count + it;
-      fs.n_static = F;
-      tm.begin(NBFD_KERNEL_CHECK, active, s);
-      if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1), "check kernel"))) break;
-      tm.end(s);
-      tm.begin(NBFD_KERNEL_VAR, active, s);
-      if ((st = check_cuda(launch_var(c, fs, form, llr, w.c2v, w.v2c, symbols, w.fsyn, s),
-                           "variable kernel")))
-        break;
-      tm.end(s);
-      tm.begin(NBFD_KERNEL_SYNDROME, active, s);
-      if ((st = check_cuda(launch_stop(c, fs, symbols, w.fsyn, it, max_iter, w.list[(it + 1) & 1],
-                                       w.count + it + 1, ok, iters, w.stats, s),
-                           "stop kernel")))
-        break;
-      tm.end(s);
-      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.count + it + 1, sizeof(int32_t),
+    int it = 1;
+    while (st == NBFD_OK && it <= max_iter && active > 0) {
+      const int last = it + kSyncEvery - 1 < max_iter ? it + kSyncEvery - 1 : max_iter;
+      for (; it <= last; ++it) {
+        FrameSet fs;
+        fs.list = w.list[it & 1];
+        fs.count = w.count + it;
+        fs.n_static = static_cast<int>(active);
+        tm.begin(NBFD_KERNEL_CHECK, it, s);
+        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1), "check kernel")))
+          break;
+        tm.end(s);
+        tm.begin(NBFD_KERNEL_VAR, it, s);
+        if ((st = check_cuda(launch_var(c, fs, form, llr, w.c2v, w.v2c, symbols, w.fsyn, s,
+                                        w.stats + 1),
+                             "variable kernel")))
+          break;
+        tm.end(s);
+        tm.begin(NBFD_KERNEL_SYNDROME, it, s);
+        if ((st = check_cuda(launch_stop(c, fs, symbols, w.fsyn, it, max_iter,
+                                         w.list[(it + 1) & 1], w.count + it + 1, ok, iters,
+                                         w.stats, s),
+                             "stop kernel")))
+          break;
+        tm.end(s);
+      }
+      if (st) break;
+      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.count + it, sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s),
                            "cudaMemcpyAsync(count)")))
         break;
       if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
-      tm.flush();
       active = *host_count;
     }
     if (st == NBFD_OK) {
@@ -229,8 +252,15 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       if (*host_count != 0)
         st = set_error(NBFD_ETIMEDOUT, "a bounded device-side wait expired (status %d)", *host_count);
     }
+    if (st == NBFD_OK && tm.on()) {
+      std::vector<int32_t> counts((size_t)max_iter + 2, 0);
+      if ((st = check_cuda(cudaMemcpy(counts.data(), w.count, counts.size() * 4,
+                                      cudaMemcpyDeviceToHost),
+                           "cudaMemcpy(counts)")))
+        break;
+      tm.flush(counts, F);
+    }
   } while (false);
-  tm.flush();
   if (host_count) cudaFreeHost(host_count);
   if (owned) cudaFreeAsync(workspace, s);
   return st;

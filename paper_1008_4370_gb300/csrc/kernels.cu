@@ -362,15 +362,27 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
 }
 
 bool form_supported(int form, int m) {
-  (void)m;
-  return form == NBFD_FORM_FP32_DIRECT || form == NBFD_FORM_FP32_FWHT;
+  switch (form) {
+    case NBFD_FORM_FP32_DIRECT:
+    case NBFD_FORM_FP32_FWHT:
+      return true;
+    case NBFD_FORM_BF16_HGEMM:
+    case NBFD_FORM_FP16_HGEMM:
+    case NBFD_FORM_FP32_TC:
+      return m == 8;
+    default:
+      return false;
+  }
 }
 
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn,
-                       cudaStream_t s) {
+                       cudaStream_t s, int32_t *err) {
   if (!form_supported(form, c->m)) return cudaErrorNotSupported;
-  if (form == NBFD_FORM_FP32_FWHT) return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, s);
+  if (form == NBFD_FORM_FP32_FWHT)
+    return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s);
+  if (form == NBFD_FORM_BF16_HGEMM || form == NBFD_FORM_FP16_HGEMM || form == NBFD_FORM_FP32_TC)
+    return launch_var_tc(c, fs, form, llr, c2v, v2c, sym, fsyn, err, s);
   const long long total = (long long)fs.n_static * c->N;
 #define NBFD_VAR(MB)                                                                       \
   {                                                                                        \

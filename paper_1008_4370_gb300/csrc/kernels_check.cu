@@ -2,7 +2,7 @@
 //
 // A check's k slots are one contiguous block of k*q floats ([slot][z], slots check-major), and
 // consecutive checks of a frame are contiguous too. A block owns a sequence of stages of T
-// checks; thread 0 streams the next S-1 stages into shared memory with cp.async.bulk (the bulk
+// checks; thread 0 streams the next S-2 stages into shared memory with cp.async.bulk (the bulk
 // copy engine, completion counted on one mbarrier per stage) while all 256 threads work on the
 // current stage in place: thread (i, z) gathers entry H_e z of every slot e of its check, forms
 // the leave-one-out Gamma sums (prefix and suffix passes: no subtraction, so +inf magnitudes
@@ -16,77 +16,13 @@
 
 #include <cstdint>
 
+#include "bulk_copy.cuh"
 #include "device_common.cuh"
 #include "nbfd_internal.h"
 
 namespace nbfd {
 
 namespace {
-
-constexpr long long kWaitBudgetCycles = 4000000000LL;  // ~2 s at the maximum SM clock
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for phase `parity` of `bar`; false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudgetCycles) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes,
-                                          uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_addr(dst_smem)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-               "r"(smem_addr(src_smem)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_all() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 __device__ __forceinline__ int n_frames_of(const FrameSet &fs) {
   return fs.list ? __ldg(fs.count) : fs.n_static;
@@ -153,7 +89,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   long long issued = 0;  // stages whose loads thread 0 has issued (meaningful in thread 0)
   if (threadIdx.x == 0) {
-    for (; issued < S - 1 && issued < my_count; ++issued) {
+    for (; issued < S - 2 && issued < my_count; ++issued) {
       const long long st = my_first + issued * gridDim.x;
       const int bi = static_cast<int>(issued % S);
       const long long first = st * T;
@@ -168,11 +104,12 @@ __global__ void __launch_bounds__(256)
   for (; i < my_count; ++i) {
     const int b = static_cast<int>(i % S);
     const long long st = my_first + i * gridDim.x;
-    // prefetch stage i+S-1 into the buffer stage i-1 used, once its store has read it
+    // prefetch stage i+S-2 into the buffer stage i-2 used, once that stage's store has read it
+    // (the store of stage i-1 may still be reading its own buffer)
     if (threadIdx.x == 0 && issued < my_count) {
       const long long stj = my_first + issued * gridDim.x;
       const int bj = static_cast<int>(issued % S);
-      bulk_wait_read_all();
+      bulk_wait_read_all_but_one();
       const long long first = stj * T;
       const long long n = (first + T < total ? T : total - first);
       mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n) * k * Q * 4u);
@@ -252,7 +189,7 @@ cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c,
   int g = (16 * 1024) / (ipb * k * Q * 4);
   if (g < 1) g = 1;
   const int T = ipb * g;
-  const int S = (size_t)T * k * Q * 4 > 24 * 1024 ? 3 : 4;
+  const int S = (size_t)T * k * Q * 4 > 24 * 1024 ? 4 : 5;
   const size_t smem = 128 + (size_t)S * T * k * Q * 4;
   const long long total = (long long)fs.n_static * c->M;
   const long long n_stages = (total + T - 1) / T;

@@ -14,6 +14,7 @@
 
 #include <cstdint>
 
+#include "bulk_copy.cuh"
 #include "device_common.cuh"
 #include "nbfd_internal.h"
 
@@ -65,42 +66,100 @@ __device__ __forceinline__ int frame_of(const FrameSet &fs, long long slot) {
 
 }  // namespace
 
+// Per warp, two stages of shared memory hold the two check messages of the warp's VPW
+// variables; lane 0 resolves the next variables' frame and edge indices and brings their
+// messages in with cp.async.bulk (one mbarrier per stage, bounded waits) while the warp
+// transforms the current ones.
+template <int MB>
+struct VarStage {
+  static constexpr int Q = 1 << MB;
+  static constexpr int VPW = ChannelLayout<MB>::VPW;
+  float msg[2][VPW][2][Q];  // [stage][variable][edge 1, edge 2][z]
+  int4 idx[2][VPW];         // [stage][variable] = (frame, variable, slot e1, slot e2)
+  float m[VPW][Q];          // M of each variable, for the read-out
+  uint64_t bar[2];
+};
+
+template <int MB>
+__device__ __forceinline__ void var_issue(VarStage<MB> &ws, int st, long long base, long long total,
+                                          int N, int E, const FrameSet &fs,
+                                          const int32_t *__restrict__ var_edges,
+                                          const float *__restrict__ c2v) {
+  constexpr int Q = VarStage<MB>::Q, VPW = VarStage<MB>::VPW;
+  uint32_t bytes = 0;
+  for (int g = 0; g < VPW; ++g) {
+    const long long item = base + g;
+    // past the end: a valid stand-in so that every index the warp uses stays in bounds
+    const long long it = item < total ? item : 0;
+    const long long slot = it / N;
+    const int v = static_cast<int>(it - slot * N);
+    const int f = frame_of(fs, slot);
+    ws.idx[st][g] = make_int4(f, v, __ldg(var_edges + 2 * v), __ldg(var_edges + 2 * v + 1));
+    if (item < total) bytes += 2u * Q * 4u;
+  }
+  mbar_expect_tx(&ws.bar[st], bytes);
+  for (int g = 0; g < VPW; ++g) {
+    if (base + g >= total) break;
+    const int4 ix = ws.idx[st][g];
+    bulk_load(ws.msg[st][g][0], c2v + ((size_t)ix.x * E + ix.z) * Q, Q * 4u, &ws.bar[st]);
+    bulk_load(ws.msg[st][g][1], c2v + ((size_t)ix.x * E + ix.w) * Q, Q * 4u, &ws.bar[st]);
+  }
+}
+
 template <int MB>
 __global__ void __launch_bounds__(256, 3)
     k_var_fwht(const float *__restrict__ llr, const float *__restrict__ c2v,
                float *__restrict__ v2c, uint16_t *__restrict__ sym, uint8_t *__restrict__ fsyn,
                const int32_t *__restrict__ var_edges, const uint8_t *__restrict__ edge_h,
-               const uint8_t *__restrict__ perm, int N, int E, FrameSet fs) {
+               const uint8_t *__restrict__ perm, int N, int E, FrameSet fs, int32_t *err) {
   using CL = ChannelLayout<MB>;
   constexpr int Q = CL::Q, VPT = CL::VPT, LPV = CL::LPV, VPW = CL::VPW;
-  __shared__ float sM[8][VPW * Q];  // M of each variable of the warp, for the read-out
+  __shared__ VarStage<MB> stage_mem[8];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  VarStage<MB> &ws = stage_mem[wib];
   const int sub = lane / LPV, l = lane % LPV;
   const long long total = (long long)frames_in(fs) * N;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = gw * VPW; base < total; base += nw * VPW) {
+  if (gw * VPW >= total) return;
+  if (lane == 0) {
+    mbar_init(&ws.bar[0], 1);
+    mbar_init(&ws.bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    var_issue<MB>(ws, 0, gw * VPW, total, N, E, fs, var_edges, c2v);
+  }
+  __syncwarp();
+  long long t = 0;
+  bool failed = false, next_issued = false;
+  for (long long base = gw * VPW; base < total; base += nw * VPW, ++t) {
+    const int b = static_cast<int>(t & 1);
+    const long long next = base + nw * VPW;
+    next_issued = next < total;
+    if (lane == 0 && next_issued) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      var_issue<MB>(ws, b ^ 1, next, total, N, E, fs, var_edges, c2v);
+    }
+    const bool ok = mbar_wait_bounded(&ws.bar[b], static_cast<uint32_t>((t >> 1) & 1));
+    if (__any_sync(kFull, !ok)) {
+      failed = true;
+      break;
+    }
     const long long item = base + sub;
     const bool valid = item < total;
-    const long long ic = valid ? item : total - 1;
-    const long long slot = ic / N;
-    const int v = static_cast<int>(ic - slot * N);
-    const int f = frame_of(fs, slot);
-    const int e1 = __ldg(var_edges + 2 * v), e2 = __ldg(var_edges + 2 * v + 1);
+    const int4 ix = ws.idx[b][sub];
+    const int f = ix.x, v = ix.y, e1 = ix.z, e2 = ix.w;
     float c1[VPT], c2[VPT];
-    ld_global<VPT>(c1, c2v + ((size_t)f * E + e1) * Q + l * VPT);
-    ld_global<VPT>(c2, c2v + ((size_t)f * E + e2) * Q + l * VPT);
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
-      c1[j] = gamma_decode_fast(c1[j]);
-      c2[j] = gamma_decode_fast(c2[j]);
+      c1[j] = gamma_decode_fast(ws.msg[b][sub][0][l * VPT + j]);
+      c2[j] = gamma_decode_fast(ws.msg[b][sub][1][l * VPT + j]);
     }
     wht_inplace<MB>(c1, l);  // q * (x-domain check message of e1)
     wht_inplace<MB>(c2, l);
     float p[VPT];
     channel_probs_shared<MB>(llr + ((size_t)f * N + v) * MB, l, p);  // x-domain channel message
     // M_v = p0 . c1x . c2x (all checks), read out below from shared memory
-    float *m_sh = sM[wib] + sub * Q;
+    float *m_sh = ws.m[sub];
     float nm;
     {
       float mm[VPT];
@@ -137,10 +196,10 @@ __global__ void __launch_bounds__(256, 3)
     uint32_t word = 0;
 #pragma unroll
     for (int r = 0; r < (3 * MB + LPV - 1) / LPV; ++r) {
-      const int t = r * LPV + l;
+      const int tt = r * LPV + l;
       bool neg_pt = false;
-      if (t < 3 * MB) {
-        const int kind = t / MB, i = t - kind * MB;
+      if (tt < 3 * MB) {
+        const int kind = tt / MB, i = tt - kind * MB;
         const int z = kind == 0 ? (1 << i) : __ldg(perm + (kind == 1 ? h1 : h2) * Q + (1 << i));
         neg_pt = m_sh[z] < 0.0f;
       }
@@ -159,10 +218,17 @@ __global__ void __launch_bounds__(256, 3)
     }
     __syncwarp();
   }
+  if (failed && lane == 0) {
+    if (err) atomicExch(err, NBFD_ETIMEDOUT);
+    // the prefetch of the next stage may still be landing in this warp's shared memory
+    if (next_issued)
+      mbar_wait_bounded(&ws.bar[(t + 1) & 1], static_cast<uint32_t>(((t + 1) >> 1) & 1));
+  }
 }
 
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
-                            float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s) {
+                            float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
+                            cudaStream_t s) {
   const long long total = (long long)fs.n_static * c->N;
   const long long cap = (long long)sm_count() * 8;
 #define NBFD_VAR_FWHT(MB)                                                                   \
@@ -172,7 +238,7 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
     if (g > cap) g = cap;                                                                   \
     if (g < 1) g = 1;                                                                       \
     k_var_fwht<MB><<<(int)g, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,         \
-                                          c->d_edge_h, c->d_perm, c->N, c->E, fs);          \
+                                          c->d_edge_h, c->d_perm, c->N, c->E, fs, err);     \
   }
   switch (c->m) {
     case 2: NBFD_VAR_FWHT(2) break;

@@ -47,7 +47,8 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
 cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
                               int32_t *err, cudaStream_t s);
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
-                       const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s);
+                       const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s,
+                       int32_t *err = nullptr);
 cudaError_t launch_syndrome(const nbfd_code *c, int F, const uint16_t *sym, const uint8_t *fsyn,
                             uint16_t *fourier, uint16_t *exact, cudaStream_t s);
 // Stop test + compaction of one decoding iteration (see decode.cu).
@@ -55,7 +56,11 @@ cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, co
                         int iter, int max_iter, int32_t *next_list, int32_t *next_count,
                         uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s);
 bool form_supported(int form, int m);
+cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float *llr,
+                          const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
+                          cudaStream_t s);
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
-                            float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s);
+                            float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
+                            cudaStream_t s);
 
 }  // namespace nbfd

@@ -61,7 +61,8 @@ def compare(gpu: np.ndarray, s_o: np.ndarray, l_o: np.ndarray, kappa=None, lin_a
     mask = (np.abs(P_o) >= LOG_FLOOR) & well
     sg, lg = decode_pair(gpu)
     logerr = float(np.max(np.abs(lg[mask] - l_o[mask]))) if mask.any() else 0.0
-    sign_bad = int(np.sum(sg[mask] != s_o[mask]))
+    sign_mask = np.abs(P_o) > np.maximum(2 * tol, LOG_FLOOR)  # a sign is decided where |P| > error
+    sign_bad = int(np.sum(sg[sign_mask] != s_o[sign_mask]))
     nan = int(np.isnan(gpu).sum())
     ok = lin_bad == 0 and logerr <= log_atol and sign_bad == 0 and nan == 0
     return ok, {"lin_max": lin, "lin_bad": lin_bad, "log_max": logerr, "sign_bad": sign_bad, "nan": nan,

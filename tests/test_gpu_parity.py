@@ -124,10 +124,26 @@ def test_check_parity(dev, spec):
 
 
 FORMS = [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT]
+TC_FORMS = [nb.FORM_BF16_HGEMM, nb.FORM_FP16_HGEMM, nb.FORM_FP32_TC]
+# unit roundoff of the operands each form rounds to (FP32 forms: 2^-24)
+FORM_UNIT = {nb.FORM_FP32_DIRECT: 2.0 ** -24, nb.FORM_FP32_FWHT: 2.0 ** -24, nb.FORM_FP32_TC: 2.0 ** -24,
+             nb.FORM_BF16_HGEMM: 2.0 ** -9, nb.FORM_FP16_HGEMM: 2.0 ** -12}
+VAR_CASES = ([(sp, f) for sp in STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6"] for f in FORMS]
+             + [(sp, f) for sp in [(8, 16, 4, 25), (8, 64, 16, 27), "gf256_n512_k4"] for f in TC_FORMS])
 
 
-@pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("spec", STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6"])
+def _tolerances(form):
+    """(linear floor, kappa factor, log bound, decision margin) for a form: the FP32 forms use the
+    FP32 bounds of helpers.py; the BF16 / FP16 operand forms a bound scaled by their unit
+    roundoff u_p: |dP| <= max(16 u_p, 4 u_p kappa), decisions compared where the FP64 margin
+    exceeds 0.1."""
+    u = FORM_UNIT[form]
+    if u == 2.0 ** -24:
+        return None, None, 1e-4, MARGIN
+    return 16 * u, 4 * u, 1e9, 0.1
+
+
+@pytest.mark.parametrize("spec,form", VAR_CASES)
 def test_var_parity(dev, spec, form):
     c = _code(spec)
     oc = OracleCode.from_dict(c)
@@ -153,14 +169,19 @@ def test_var_parity(dev, spec, form):
         vs = np.arange(oc.N) if vars_ is None else np.array(vars_)
         es = np.concatenate([oc.C[v] for v in vs])
         kappa = var_conditions(oc, lam0, c2v_o)
-        ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es])
+        floor, kf, logb, margin = _tolerances(form)
+        if floor is None:
+            ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es])
+        else:
+            ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es] * kf / 2.0 ** -24, lin_atol=floor,
+                             log_atol=logb)
         assert ok, (f, st)
         M = LF.tentative(oc, lam0, c2v_o, vars=vs)
         x = LF.bit_decisions(oc, M)
         w = LF.fourier_syndrome_words(oc, M)
         marg = vn_margins(oc, M)
         for v in vs:
-            if marg[v] > MARGIN:
+            if marg[v] > margin:
                 n_cmp += 1
                 assert gs[f, v] == x[v], (f, v)
                 for e in oc.C[v]:
@@ -265,7 +286,7 @@ def test_decode_edge_cases(dev):
     assert ei.value.status == -10
 
 
-@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("form", FORMS + [nb.FORM_FP32_TC])
 def test_decode_full_size_gf256_n512(dev, form):
     """The measured configuration: GF(256) (2,4) N=512, 1024 frames at Eb/N0 = 1.5 dB. With at
     most 4 iterations two sampled frames are decoded by the oracle as well; with 100 iterations
@@ -288,3 +309,35 @@ def test_decode_full_size_gf256_n512(dev, form):
     assert ok_h.mean() > 0.5
     it_h = it.cpu().numpy()
     assert it_h.min() >= 1 and it_h.max() <= 100 and np.all(it_h[~ok_h] == 100)
+
+
+@pytest.mark.parametrize("form", [nb.FORM_BF16_HGEMM, nb.FORM_FP16_HGEMM])
+def test_decode_low_precision_forms_gf256_n512(dev, form):
+    """BF16 / FP16 operand forms on the measured configuration: properties at any size (frames
+    flagged decoded satisfy H x = 0 and carry the transmitted codeword) and a frame error rate
+    close to the FP32 form's on the same frames."""
+    c = synth.named_code("gf256_n512_k4")
+    tx, llr = synth.frames(c, 1024, 1.5)
+    code = nb.Code(c)
+    x = _t(llr, dev)
+    sym, ok, it = nb.decode(code, x, 100, form)
+    ex = torch.empty((1024, code.M), dtype=torch.int16, device=dev)
+    nb.nbfd_syndrome(code.handle, 1024, sym, None, None, ex)
+    _, ok32, _ = nb.decode(code, x, 100, nb.FORM_FP32_FWHT)
+    torch.cuda.synchronize()
+    ok_h = ok.cpu().numpy().astype(bool)
+    assert np.array_equal(ok_h, ~ex.cpu().numpy().any(axis=1))
+    sym_h = sym.cpu().numpy().astype(np.int64)
+    assert np.mean(np.all(sym_h[ok_h] == tx[ok_h], axis=1)) > 0.999
+    fer, fer32 = 1 - ok_h.mean(), 1 - ok32.cpu().numpy().mean()
+    assert fer <= 3 * fer32 + 0.02, (fer, fer32)
+
+
+def test_tc_forms_need_m8(dev):
+    c = synth.named_code("gf16_n32_k4")
+    code = nb.Code(c)
+    _, llr = synth.frames(c, 4, 2.0)
+    for form in TC_FORMS:
+        with pytest.raises(nb.NbfdError) as ei:
+            nb.decode(code, _t(llr, dev), 5, form)
+        assert ei.value.status == -10
