@@ -156,6 +156,13 @@ __global__ void __launch_bounds__(256, 3)
     }
     wht_inplace<MB>(c1, l);  // q * (x-domain check message of e1)
     wht_inplace<MB>(c2, l);
+    // x-domain messages are probability vectors (non-negative in exact arithmetic): drop the
+    // negative rounding noise of the transform
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+      c1[j] = fmaxf(c1[j], 0.0f);
+      c2[j] = fmaxf(c2[j], 0.0f);
+    }
     float p[VPT];
     channel_probs_shared<MB>(llr + ((size_t)f * N + v) * MB, l, p);  // x-domain channel message
     // M_v = p0 . c1x . c2x (all checks), read out below from shared memory
@@ -174,19 +181,21 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
     for (int j = 0; j < VPT; ++j) c2[j] *= p[j];
     wht_inplace<MB>(c2, l);
-    const float r1 = 1.0f / __shfl_sync(kFull, c2[0], sub * LPV);
+    const float n1 = __shfl_sync(kFull, c2[0], sub * LPV);
+    const float r1 = n1 > 0.0f ? 1.0f / n1 : 0.0f;  // U(0) <= 0 only by underflow: send delta_0
     if (valid) {
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) c2[j] = gamma_encode_fast(c2[j] * r1);
+      for (int j = 0; j < VPT; ++j) c2[j] = gamma_encode_fast((l == 0 && j == 0) ? 1.0f : c2[j] * r1);
       st_global<VPT>(v2c + ((size_t)f * E + e1) * Q + l * VPT, c2);
     }
 #pragma unroll
     for (int j = 0; j < VPT; ++j) c1[j] *= p[j];
     wht_inplace<MB>(c1, l);
-    const float r2 = 1.0f / __shfl_sync(kFull, c1[0], sub * LPV);
+    const float n2 = __shfl_sync(kFull, c1[0], sub * LPV);
+    const float r2 = n2 > 0.0f ? 1.0f / n2 : 0.0f;
     if (valid) {
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) c1[j] = gamma_encode_fast(c1[j] * r2);
+      for (int j = 0; j < VPT; ++j) c1[j] = gamma_encode_fast((l == 0 && j == 0) ? 1.0f : c1[j] * r2);
       st_global<VPT>(v2c + ((size_t)f * E + e2) * Q + l * VPT, c1);
     }
     // TENTATIVE: signs of M at alpha^{i-1} (t < MB), H_e1 alpha^{i-1} (t < 2MB) and

@@ -277,6 +277,13 @@ __global__ void __launch_bounds__(256, 3)
     }
     wht256_tc<P>(c1, hb);
     wht256_tc<P>(c2, hb);
+    // x-domain messages are probability vectors (non-negative in exact arithmetic): drop the
+    // negative rounding noise of the transform
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      c1[r] = fmaxf(c1[r], 0.0f);
+      c2[r] = fmaxf(c2[r], 0.0f);
+    }
     // channel probabilities p0(x) at the transposed positions: low nibble g + 8h, high 8j+2t+c
     float pr[8];
     {
@@ -320,21 +327,25 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
     for (int r = 0; r < 8; ++r) c2[r] *= pr[r];
     wht256_tc<P>(c2, hb);
-    const float r1 = 1.0f / __shfl_sync(kFull, c2[0], 0);
+    const float n1 = __shfl_sync(kFull, c2[0], 0);
+    const float r1 = n1 > 0.0f ? 1.0f / n1 : 0.0f;  // U(0) <= 0 only by underflow: send delta_0
     float *o1 = v2c + ((size_t)f * E + e1) * Q;
 #pragma unroll
     for (int r = 0; r < 8; r += 2)
       *reinterpret_cast<float2 *>(o1 + z_natural(r, g, t)) =
-          make_float2(gamma_encode_fast(c2[r] * r1), gamma_encode_fast(c2[r + 1] * r1));
+          make_float2(gamma_encode_fast((r == 0 && lane == 0) ? 1.0f : c2[r] * r1),
+                      gamma_encode_fast(c2[r + 1] * r1));
 #pragma unroll
     for (int r = 0; r < 8; ++r) c1[r] *= pr[r];
     wht256_tc<P>(c1, hb);
-    const float r2 = 1.0f / __shfl_sync(kFull, c1[0], 0);
+    const float n2 = __shfl_sync(kFull, c1[0], 0);
+    const float r2 = n2 > 0.0f ? 1.0f / n2 : 0.0f;
     float *o2 = v2c + ((size_t)f * E + e2) * Q;
 #pragma unroll
     for (int r = 0; r < 8; r += 2)
       *reinterpret_cast<float2 *>(o2 + z_natural(r, g, t)) =
-          make_float2(gamma_encode_fast(c1[r] * r2), gamma_encode_fast(c1[r + 1] * r2));
+          make_float2(gamma_encode_fast((r == 0 && lane == 0) ? 1.0f : c1[r] * r2),
+                      gamma_encode_fast(c1[r + 1] * r2));
     // TENTATIVE: signs of M at alpha^{i-1}, H_e1 alpha^{i-1}, H_e2 alpha^{i-1} (lane = point)
     __syncwarp();
     bool neg_pt = false;
