@@ -118,7 +118,7 @@ size_t nbfd_decode_workspace_size(const nbfd_code *code, int n_frames, int max_i
  *   iters_dev       : [F] int32 out: iteration at which the frame stopped (max_iter if never).
  *   workspace_dev   : device scratch of >= nbfd_decode_workspace_size() bytes, 256-byte
  *                     aligned; NULL makes the call allocate and free it on `cuda_stream`.
- * The call is stream-ordered but synchronises with `cuda_stream` once per iteration to test
+ * The call is stream-ordered but synchronises with `cuda_stream` every few iterations to test
  * for early termination (it returns after the last iteration's kernels completed).
  * Errors: NBFD_EINVAL, NBFD_ENOTSUP, NBFD_ENOMEM, NBFD_ECUDA.
  */
@@ -203,6 +203,39 @@ int nbfd_var_update(const nbfd_code *code, int n_frames, int form, const float *
 int nbfd_syndrome(const nbfd_code *code, int n_frames, const uint16_t *symbols_dev,
                   const uint8_t *fsyn_dev, uint16_t *fourier_dev, uint16_t *exact_dev,
                   void *cuda_stream);
+
+/* ---- serving: continuous batching of single-frame requests ----------------------------
+ * The decoding of Section 2 / Section 3.2 applied to a stream of requests: a worker thread keeps
+ * one pool of resident frame slots per code (messages of both directions stay in device memory
+ * across iterations), admits queued requests into free slots between rounds, runs one decoding
+ * iteration per round over every pool (pools on separate streams overlap on the device), and
+ * retires each frame as soon as its Fourier-domain and GF(2^m) syndromes are zero or its own
+ * max_iter is reached. A frame's result does not depend on the other frames in flight. */
+typedef struct nbfd_server nbfd_server;
+
+/* Start a server on the current device. mem_budget_bytes bounds the device memory of all pools
+ * (a pool is sized from what is left when its code is first submitted, at most 4096 slots);
+ * form is an NBFD_FORM_* for every request. */
+int nbfd_srv_create(size_t mem_budget_bytes, int form, nbfd_server **out);
+
+/* Queue one frame: llr_host [N][m] float32 (copied), max_iter >= 1. *ticket identifies it.
+ * NBFD_EBUSY: no pool fits the remaining budget or the queue is full -- retry later.
+ * NBFD_ENOTSUP: the server's form does not support this code's m. */
+int nbfd_srv_submit(nbfd_server *srv, const nbfd_code *code, const float *llr_host, int max_iter,
+                    uint64_t *ticket);
+
+/* Returns 1 and fills the outputs (symbols_host [N] uint16, *ok, *iters, *latency_s = seconds
+ * from submit to retirement; any may be NULL) once the ticket's frame retired, 0 while it is
+ * queued or in flight, < 0 for an unknown ticket or a server error. A ticket is reported once. */
+int nbfd_srv_poll(nbfd_server *srv, uint64_t ticket, uint16_t *symbols_host, uint8_t *ok,
+                  int32_t *iters, double *latency_s);
+
+/* Rounds run so far, frames queued and in flight, device bytes held by pools. */
+int nbfd_srv_stats(nbfd_server *srv, long long *rounds, long long *queued, long long *in_flight,
+                   size_t *device_bytes);
+
+/* Stop the worker and free the pools (pending requests are dropped). */
+void nbfd_srv_destroy(nbfd_server *srv);
 
 /* ---- kernel timers (CUDA events around every launch of nbfd_decode) -------------------- */
 #define NBFD_KERNEL_INIT 0

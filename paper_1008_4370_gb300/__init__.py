@@ -19,7 +19,8 @@ __all__ = [
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
-    "nbfd_last_error", "nbfd_status_string", "Code", "decode",
+    "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
+    "nbfd_srv_poll", "nbfd_srv_stats", "nbfd_srv_destroy",
 ]
 
 FORM_FP32_DIRECT = 0
@@ -51,6 +52,11 @@ SIGNATURES = [
     ("nbfd_check_update", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_var_update", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
     ("nbfd_syndrome", _I, [_P, _I, _P, _P, _P, _P, _P]),
+    ("nbfd_srv_create", _I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    ("nbfd_srv_submit", _I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_uint64)]),
+    ("nbfd_srv_poll", _I, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("nbfd_srv_stats", _I, [_P, _P, _P, _P, _P]),
+    ("nbfd_srv_destroy", None, [_P]),
     ("nbfd_prof_enable", _I, [_I]),
     ("nbfd_prof_get", _I, [_I, _P, _P, _P]),
     ("nbfd_last_error", ctypes.c_char_p, []),
@@ -195,6 +201,44 @@ def nbfd_var_update(handle, n_frames, form, llr, c2v, v2c, symbols=None, fsyn=No
 def nbfd_syndrome(handle, n_frames, symbols, fsyn, fourier, exact, stream=None):
     _check(lib().nbfd_syndrome(handle, int(n_frames), _dptr(symbols), _dptr(fsyn), _dptr(fourier),
                                _dptr(exact), _stream(stream)))
+
+
+def nbfd_srv_create(mem_budget_bytes, form):
+    h = ctypes.c_void_p()
+    _check(lib().nbfd_srv_create(int(mem_budget_bytes), int(form), ctypes.byref(h)))
+    return h.value
+
+
+def nbfd_srv_submit(srv, code_handle, llr_host, max_iter):
+    x = np.ascontiguousarray(llr_host, dtype=np.float32)
+    t = ctypes.c_uint64()
+    _check(lib().nbfd_srv_submit(srv, code_handle, x.ctypes.data, int(max_iter), ctypes.byref(t)))
+    return t.value
+
+
+def nbfd_srv_poll(srv, ticket, n_symbols):
+    """None while pending, else (symbols uint16 array, ok, iters, latency_s)."""
+    sym = np.empty(n_symbols, dtype=np.uint16)
+    ok = ctypes.c_uint8()
+    it = ctypes.c_int32()
+    lat = ctypes.c_double()
+    r = lib().nbfd_srv_poll(srv, ctypes.c_uint64(ticket), sym.ctypes.data, ctypes.byref(ok), ctypes.byref(it),
+                            ctypes.byref(lat))
+    if r < 0:
+        _check(r)
+    if r == 0:
+        return None
+    return sym, ok.value, it.value, lat.value
+
+
+def nbfd_srv_stats(srv):
+    vals = [ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()]
+    _check(lib().nbfd_srv_stats(srv, *[ctypes.byref(v) for v in vals]))
+    return tuple(v.value for v in vals)
+
+
+def nbfd_srv_destroy(srv):
+    lib().nbfd_srv_destroy(srv)
 
 
 def nbfd_prof_enable(on: bool):
