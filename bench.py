@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--batches", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16384, help="requests of the serving leg (0: skip)")
+    ap.add_argument("--serve-load", type=float, default=30000.0, help="Poisson offered load, frames/s")
+    ap.add_argument("--serve-sweep", action="store_true", help="serving sweep over loads and the code mix")
     return ap.parse_args()
 
 
@@ -211,6 +214,99 @@ def reference_mean_iterations():
     return None
 
 
+def serve_run(nb, streams, form, budget, poll_sleep=2e-4, timeout=300.0):
+    """Drive the serving loop. streams: list of (code, llr [R][N][m], arrivals (s, relative, sorted)
+    or None for 'all at t = 0', max_iter, info_bits). Returns per-request (ok, iters, latency, bits)
+    plus the wall time from the first arrival to the last retirement."""
+    srv = nb.nbfd_srv_create(budget, form)
+    try:
+        t0 = nb.nbfd_srv_clock()
+        events = []  # (arrival, stream index, frame index)
+        for si, (_, llr, arr, _, _) in enumerate(streams):
+            for i in range(llr.shape[0]):
+                events.append((0.0 if arr is None else float(arr[i]), si, i))
+        events.sort()
+        total = len(events)
+        bits_of = {}
+        got = []
+        pos = 0
+        while pos < total or len(got) < total:
+            now = nb.nbfd_srv_clock() - t0
+            # submit every request that has arrived, per stream in one call
+            end = pos
+            while end < total and events[end][0] <= now:
+                end += 1
+            if end > pos:
+                by = {}
+                for arr_t, si, i in events[pos:end]:
+                    by.setdefault(si, []).append((arr_t, i))
+                for si, lst in by.items():
+                    code, llr, _, max_iter, bits = streams[si]
+                    idx = np.array([i for _, i in lst])
+                    tk = nb.nbfd_srv_submit_many(srv, code.handle, llr[idx], max_iter,
+                                                 np.array([t0 + t for t, _ in lst]))
+                    for t in tk.tolist():
+                        bits_of[t] = bits
+                pos = end
+            tk, ok, it, lat = nb.nbfd_srv_collect(srv, 65536)
+            for j in range(len(tk)):
+                got.append((int(ok[j]), int(it[j]), float(lat[j]), bits_of[int(tk[j])]))
+            if now > timeout:
+                raise TimeoutError("serving run did not finish")
+            if len(tk) == 0:
+                time.sleep(poll_sleep)
+        wall = nb.nbfd_srv_clock() - t0
+    finally:
+        nb.nbfd_srv_destroy(srv)
+    return got, wall
+
+
+def serve_summary(got, wall, offered=None):
+    lat = np.array([g[2] for g in got])
+    bits = sum(g[3] for g in got)
+    return {"requests": len(got), "mbit_s": bits / wall / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "fer": float(np.mean([1 - g[0] for g in got])),
+            "mean_iterations": float(np.mean([g[1] for g in got])), "offered_frames_s": offered,
+            "wall_s": wall}
+
+
+def run_serve_sweep(a):
+    """Serving sweep of the configured mix: Poisson arrivals drawn from five codes (weights
+    .1/.3/.2/.3/.1), per-request Eb/N0 uniform in 1.5-3.5 dB, max 100 iterations."""
+    import torch
+
+    import paper_1008_4370_gb300 as nb
+    from paper_1008_4370_gb300 import build as nbuild
+
+    nbuild.build()
+    torch.cuda.init()
+    mix = [("gf16_n96_k4", 0.1), ("gf64_n1200_k6", 0.3), ("gf64_n4096_k8", 0.2), ("gf256_n512_k4", 0.3),
+           ("gf256_n2048_k16", 0.1)]
+    codes = {}
+    for name, _ in mix:
+        c = synth.named_code(name)
+        enc = synth.Encoder(c)
+        codes[name] = (c, nb.Code(c), enc.info_symbols * c["m"], enc)
+    for lam in [1e4, 3e4, 1e5, 3e5, 1e6]:
+        dur = min(1.0, max(0.2, 20000.0 / lam))
+        rng = synth.rng_for(17, int(lam))
+        n_req = int(lam * dur)
+        arr = np.sort(rng.uniform(0.0, dur, size=n_req))
+        which = rng.choice(len(mix), size=n_req, p=[w for _, w in mix])
+        streams = []
+        for ci, (name, _) in enumerate(mix):
+            sel = np.nonzero(which == ci)[0]
+            if len(sel) == 0:
+                continue
+            c, code, bits, enc = codes[name]
+            ebn0 = rng.uniform(1.5, 3.5, size=len(sel))
+            _, llr = synth.frames(c, len(sel), ebn0, snr_idx=ci, batch_idx=int(lam) % 100000, encoder=enc)
+            streams.append((code, llr, arr[sel], 100, bits))
+        got, wall = serve_run(nb, streams, FORMS[a.form] if FORMS[a.form] in (0, 3) else FORMS["fwht"],
+                              40 << 30)
+        print(json.dumps({"serving_sweep": serve_summary(got, wall, lam), "form": a.form}), flush=True)
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -331,6 +427,21 @@ def run_ours(a):
         p_t, p_value = aggregate(p_s, F * a.plain_steps, info_bits, dist if world > 1 else None, dev)
         plain = {"form": "direct", "value": p_value, "unit": "Mbit/s", "steps": a.plain_steps,
                  "ms_per_step": 1e3 * p_t / a.plain_steps}
+    # serving leg: continuous batching of single-frame requests of this code
+    served = None
+    if a.serve_requests > 0 and world == 1:
+        R = a.serve_requests
+        pool = [batches[b][1].cpu().numpy() for b in range(len(batches))]
+        llr_all = np.concatenate(pool, axis=0)
+        reps = (R + llr_all.shape[0] - 1) // llr_all.shape[0]
+        llr_req = np.concatenate([llr_all] * reps, axis=0)[:R]
+        got, wall = serve_run(nb, [(code, llr_req, None, a.max_iter, info_bits)], form, 32 << 30)
+        sat = serve_summary(got, wall)
+        rng = synth.rng_for(23, R)
+        arr = np.cumsum(rng.exponential(1.0 / a.serve_load, size=R))
+        got2, wall2 = serve_run(nb, [(code, llr_req, arr, a.max_iter, info_bits)], form, 32 << 30)
+        ld = serve_summary(got2, wall2, a.serve_load)
+        served = {"form": a.form, "saturation": sat, "poisson": ld}
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -393,6 +504,7 @@ def run_ours(a):
         "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": F * N * m * 4,
                 "d2h_bytes_per_step": F * N * 2 + F + F * 4},
         "plain_fp32": plain,
+        "served": served,
         "gpu_launches": launches_total,
         "roofline": roof,
         "clocks": clk,
@@ -406,6 +518,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serve_sweep:
+        run_serve_sweep(a)
     else:
         run_ours(a)
 

@@ -230,6 +230,21 @@ int nbfd_srv_submit(nbfd_server *srv, const nbfd_code *code, const float *llr_ho
 int nbfd_srv_poll(nbfd_server *srv, uint64_t ticket, uint16_t *symbols_host, uint8_t *ok,
                   int32_t *iters, double *latency_s);
 
+/* Seconds on the server's monotonic clock (the clock latencies are measured on). */
+double nbfd_srv_clock(void);
+
+/* Queue n frames of one code at once: llr_host [n][N][m]; arrival (may be NULL) gives each
+ * frame's arrival time on nbfd_srv_clock() -- latency is then measured from it; tickets [n] out.
+ * Errors as nbfd_srv_submit (no frame is queued on error). */
+int nbfd_srv_submit_many(nbfd_server *srv, const nbfd_code *code, int n, const float *llr_host,
+                         int max_iter, const double *arrival, uint64_t *tickets);
+
+/* Take up to max_n retired frames in retirement order: tickets, flags, iteration counts and
+ * latencies (any array may be NULL). Returns how many were taken (0 if none), < 0 on a server
+ * error. Frames taken here are no longer reported by nbfd_srv_poll. */
+int nbfd_srv_collect(nbfd_server *srv, int max_n, uint64_t *tickets, uint8_t *ok, int32_t *iters,
+                     double *latency_s);
+
 /* Rounds run so far, frames queued and in flight, device bytes held by pools. */
 int nbfd_srv_stats(nbfd_server *srv, long long *rounds, long long *queued, long long *in_flight,
                    size_t *device_bytes);

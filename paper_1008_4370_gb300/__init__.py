@@ -20,7 +20,8 @@ __all__ = [
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
-    "nbfd_srv_poll", "nbfd_srv_stats", "nbfd_srv_destroy",
+    "nbfd_srv_poll", "nbfd_srv_stats", "nbfd_srv_destroy", "nbfd_srv_clock", "nbfd_srv_submit_many",
+    "nbfd_srv_collect",
 ]
 
 FORM_FP32_DIRECT = 0
@@ -56,6 +57,9 @@ SIGNATURES = [
     ("nbfd_srv_submit", _I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_uint64)]),
     ("nbfd_srv_poll", _I, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
     ("nbfd_srv_stats", _I, [_P, _P, _P, _P, _P]),
+    ("nbfd_srv_clock", ctypes.c_double, []),
+    ("nbfd_srv_submit_many", _I, [_P, _P, _I, _P, _I, _P, _P]),
+    ("nbfd_srv_collect", _I, [_P, _I, _P, _P, _P, _P]),
     ("nbfd_srv_destroy", None, [_P]),
     ("nbfd_prof_enable", _I, [_I]),
     ("nbfd_prof_get", _I, [_I, _P, _P, _P]),
@@ -229,6 +233,32 @@ def nbfd_srv_poll(srv, ticket, n_symbols):
     if r == 0:
         return None
     return sym, ok.value, it.value, lat.value
+
+
+def nbfd_srv_clock():
+    return float(lib().nbfd_srv_clock())
+
+
+def nbfd_srv_submit_many(srv, code_handle, llr_host, max_iter, arrival=None):
+    x = np.ascontiguousarray(llr_host, dtype=np.float32)
+    n = int(x.shape[0])
+    t = np.empty(n, dtype=np.uint64)
+    arr = None if arrival is None else np.ascontiguousarray(arrival, dtype=np.float64)
+    _check(lib().nbfd_srv_submit_many(srv, code_handle, n, x.ctypes.data, int(max_iter),
+                                      None if arr is None else arr.ctypes.data, t.ctypes.data))
+    return t
+
+
+def nbfd_srv_collect(srv, max_n=4096):
+    """(tickets, ok, iters, latency_s) of up to max_n retired frames."""
+    t = np.empty(max_n, dtype=np.uint64)
+    ok = np.empty(max_n, dtype=np.uint8)
+    it = np.empty(max_n, dtype=np.int32)
+    lat = np.empty(max_n, dtype=np.float64)
+    n = lib().nbfd_srv_collect(srv, int(max_n), t.ctypes.data, ok.ctypes.data, it.ctypes.data, lat.ctypes.data)
+    if n < 0:
+        _check(n)
+    return t[:n], ok[:n], it[:n], lat[:n]
 
 
 def nbfd_srv_stats(srv):

@@ -124,7 +124,7 @@ struct Request {
   uint64_t ticket;
   std::vector<float> llr;
   int max_iter;
-  double t_submit;
+  double t_submit;  // arrival time (server clock) latency is measured from
 };
 
 struct Result {
@@ -174,6 +174,7 @@ struct nbfd_server {
   uint64_t next_ticket = 1;
   std::map<const nbfd_code *, std::unique_ptr<nbfd::Pool>> pools;
   std::unordered_map<uint64_t, nbfd::Result> done;
+  std::deque<uint64_t> done_order;  // retirement order, for nbfd_srv_collect
   std::unordered_map<uint64_t, int> pending;  // tickets queued or in flight
   size_t queue_limit = 1 << 16;
   int error = NBFD_OK;
@@ -403,6 +404,7 @@ void worker_main(nbfd_server *srv) {
         r.iters = p->h_iters[slot];
         r.latency = t - it->second.t_submit;
         srv->done[it->second.ticket] = std::move(r);
+        srv->done_order.push_back(it->second.ticket);
         srv->pending.erase(it->second.ticket);
         p->in_flight.erase(it);
         p->free_slots.push_back(slot);
@@ -486,6 +488,58 @@ extern "C" int nbfd_srv_poll(nbfd_server *srv, uint64_t ticket, uint16_t *symbol
   if (latency_s) *latency_s = r.latency;
   srv->done.erase(it);
   return 1;
+}
+
+extern "C" double nbfd_srv_clock(void) { return now_s(); }
+
+extern "C" int nbfd_srv_submit_many(nbfd_server *srv, const nbfd_code *code, int n,
+                                    const float *llr_host, int max_iter, const double *arrival,
+                                    uint64_t *tickets) {
+  if (!srv || !code || n < 0 || (n > 0 && (!llr_host || !tickets)))
+    return set_error(NBFD_EINVAL, "bad argument");
+  if (max_iter < 1) return set_error(NBFD_EINVAL, "max_iter must be >= 1");
+  if (!form_supported(srv->form, code->m))
+    return set_error(NBFD_ENOTSUP, "the server's form does not support m = %d", code->m);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->error) return set_error(srv->error, "the server stopped after an error");
+  Pool *p = nullptr;
+  if (int st = make_pool(srv, code, &p)) return st;
+  if (p->queue.size() + (size_t)n > srv->queue_limit) return set_error(NBFD_EBUSY, "request queue full");
+  const size_t per = (size_t)code->N * code->m;
+  const double t = now_s();
+  for (int i = 0; i < n; ++i) {
+    Request r;
+    r.ticket = srv->next_ticket++;
+    r.llr.assign(llr_host + per * i, llr_host + per * (i + 1));
+    r.max_iter = max_iter;
+    r.t_submit = arrival ? arrival[i] : t;
+    tickets[i] = r.ticket;
+    srv->pending[r.ticket] = 1;
+    p->queue.push_back(std::move(r));
+  }
+  srv->cv.notify_all();
+  return NBFD_OK;
+}
+
+extern "C" int nbfd_srv_collect(nbfd_server *srv, int max_n, uint64_t *tickets, uint8_t *ok,
+                                int32_t *iters, double *latency_s) {
+  if (!srv || max_n < 0) return set_error(NBFD_EINVAL, "bad argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  int n = 0;
+  while (n < max_n && !srv->done_order.empty()) {
+    const uint64_t t = srv->done_order.front();
+    srv->done_order.pop_front();
+    auto it = srv->done.find(t);
+    if (it == srv->done.end()) continue;  // already taken by nbfd_srv_poll
+    if (tickets) tickets[n] = t;
+    if (ok) ok[n] = it->second.ok;
+    if (iters) iters[n] = it->second.iters;
+    if (latency_s) latency_s[n] = it->second.latency;
+    srv->done.erase(it);
+    ++n;
+  }
+  if (n == 0 && srv->error) return set_error(srv->error, "the server stopped after an error");
+  return n;
 }
 
 extern "C" int nbfd_srv_stats(nbfd_server *srv, long long *rounds, long long *queued,
