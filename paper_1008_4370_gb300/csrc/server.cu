@@ -120,6 +120,47 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// Admission: scatter n staged LLR frames to their slots, set each slot's max_iter, clear its
+// iteration counter.
+__global__ void k_admit(const float *__restrict__ staged, const int32_t *__restrict__ slots,
+                        const int32_t *__restrict__ maxits, int n, int per_frame,
+                        float *__restrict__ llr, int32_t *__restrict__ iter,
+                        int32_t *__restrict__ maxit) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int slot = slots[i];
+    if ((per_frame & 3) == 0) {  // rows start on 16-byte boundaries: vector copies
+      const float4 *src = reinterpret_cast<const float4 *>(staged + (size_t)i * per_frame);
+      float4 *dst = reinterpret_cast<float4 *>(llr + (size_t)slot * per_frame);
+      for (int j = threadIdx.x; j < per_frame / 4; j += blockDim.x) dst[j] = src[j];
+    } else {
+      for (int j = threadIdx.x; j < per_frame; j += blockDim.x)
+        llr[(size_t)slot * per_frame + j] = staged[(size_t)i * per_frame + j];
+    }
+    if (threadIdx.x == 0) {
+      iter[slot] = 0;
+      maxit[slot] = maxits[i];
+    }
+  }
+}
+
+// Retirement: pack the decisions, flags and iteration counts of the done slots contiguously.
+__global__ void k_gather_done(const int32_t *__restrict__ done_list,
+                              const int32_t *__restrict__ done_count,
+                              const uint16_t *__restrict__ sym, const uint8_t *__restrict__ ok,
+                              const int32_t *__restrict__ iter, int N,
+                              uint16_t *__restrict__ out_sym, uint8_t *__restrict__ out_ok,
+                              int32_t *__restrict__ out_iter) {
+  const int n = __ldg(done_count);
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int slot = done_list[i];
+    for (int j = threadIdx.x; j < N; j += blockDim.x) out_sym[(size_t)i * N + j] = sym[(size_t)slot * N + j];
+    if (threadIdx.x == 0) {
+      out_ok[i] = ok[slot];
+      out_iter[i] = iter[slot];
+    }
+  }
+}
+
 struct Request {
   uint64_t ticket;
   std::vector<float> llr;
@@ -143,6 +184,11 @@ struct Pool {
   uint16_t *sym = nullptr;
   uint8_t *fsyn = nullptr, *ok = nullptr;
   int32_t *iter = nullptr, *maxit = nullptr, *lists[2] = {nullptr, nullptr};
+  float *stage_llr = nullptr;                    // [S][N][m] admitted frames, packed
+  int32_t *stage_slot = nullptr, *stage_maxit = nullptr;  // [S]
+  uint16_t *pack_sym = nullptr;                  // [S][N] retired frames, packed
+  uint8_t *pack_ok = nullptr;                    // [S]
+  int32_t *pack_iter = nullptr;                  // [S]
   int32_t *done_list = nullptr, *cnt = nullptr;  // cnt: [0] active(list 0), [1] active(list 1),
                                                  // [2] done, [3] new-slot count, [4] error word
   int cur = 0;
@@ -186,8 +232,8 @@ namespace nbfd {
 namespace {
 
 size_t slot_bytes(const nbfd_code *c) {
-  return (size_t)2 * c->E * c->q * 4 + (size_t)c->N * c->m * 4 + (size_t)c->N * 2 + c->E + 1 +
-         5 * 4 + 64;
+  return (size_t)2 * c->E * c->q * 4 + (size_t)2 * c->N * c->m * 4 + (size_t)2 * c->N * 2 + c->E +
+         2 + 8 * 4 + 64;
 }
 
 int make_pool(nbfd_server *srv, const nbfd_code *c, Pool **out) {
@@ -198,15 +244,18 @@ int make_pool(nbfd_server *srv, const nbfd_code *c, Pool **out) {
   }
   const size_t per = slot_bytes(c);
   const size_t left = srv->budget > srv->used ? srv->budget - srv->used : 0;
-  long long S = (long long)(left / per);
+  // a pool takes at most a quarter of the budget, so that several codes can be served
+  const size_t share = srv->budget / 4 < left ? srv->budget / 4 : left;
+  long long S = (long long)(share / per);
   if (S > 4096) S = 4096;
+  if (S < 1 && left >= per) S = 1;
   if (S < 1) return set_error(NBFD_EBUSY, "memory budget exhausted: no pool for this code");
   auto p = std::make_unique<Pool>();
   p->code = c;
   p->S = static_cast<int>(S);
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t msg = al((size_t)S * c->E * c->q * 4);
-  size_t off[12], o = 0;
+  size_t off[19], o = 0;
   off[0] = o; o += msg;                                   // v2c
   off[1] = o; o += msg;                                   // c2v
   off[2] = o; o += al((size_t)S * c->N * c->m * 4);       // llr
@@ -219,6 +268,12 @@ int make_pool(nbfd_server *srv, const nbfd_code *c, Pool **out) {
   off[9] = o; o += al((size_t)S * 4);                     // list 1
   off[10] = o; o += al((size_t)S * 4);                    // done list
   off[11] = o; o += al(8 * 4);                            // counters
+  off[12] = o; o += al((size_t)S * c->N * c->m * 4);      // staged LLRs
+  off[13] = o; o += al((size_t)S * 4);                    // staged slots
+  off[14] = o; o += al((size_t)S * 4);                    // staged max_iter
+  off[15] = o; o += al((size_t)S * c->N * 2);             // packed decisions
+  off[16] = o; o += al((size_t)S);                        // packed flags
+  off[17] = o; o += al((size_t)S * 4);                    // packed iterations
   p->bytes = o;
   if (int st = check_cuda(cudaMalloc(&p->block, o), "cudaMalloc(server pool)")) return st;
   char *b = static_cast<char *>(p->block);
@@ -234,6 +289,12 @@ int make_pool(nbfd_server *srv, const nbfd_code *c, Pool **out) {
   p->lists[1] = reinterpret_cast<int32_t *>(b + off[9]);
   p->done_list = reinterpret_cast<int32_t *>(b + off[10]);
   p->cnt = reinterpret_cast<int32_t *>(b + off[11]);
+  p->stage_llr = reinterpret_cast<float *>(b + off[12]);
+  p->stage_slot = reinterpret_cast<int32_t *>(b + off[13]);
+  p->stage_maxit = reinterpret_cast<int32_t *>(b + off[14]);
+  p->pack_sym = reinterpret_cast<uint16_t *>(b + off[15]);
+  p->pack_ok = reinterpret_cast<uint8_t *>(b + off[16]);
+  p->pack_iter = reinterpret_cast<int32_t *>(b + off[17]);
   int st = check_cuda(cudaMemset(p->cnt, 0, 32), "cudaMemset");
   if (!st) st = check_cuda(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking), "stream");
   if (!st) st = check_cuda(cudaMallocHost(&p->h_llr, (size_t)S * c->N * c->m * 4), "pinned");
@@ -299,27 +360,29 @@ int round_issue(nbfd_server *srv, Pool *p, std::deque<Request> &admit) {
   const int n_new = static_cast<int>(admit.size());
   int32_t *cur = p->lists[p->cur];
   if (n_new > 0) {
+    const size_t per = (size_t)c->N * c->m;
     for (int i = 0; i < n_new; ++i) {
       const int slot = p->free_slots.back();
       p->free_slots.pop_back();
       Request &r = admit[i];
-      memcpy(p->h_llr + (size_t)slot * c->N * c->m, r.llr.data(), r.llr.size() * 4);
-      cudaMemcpyAsync(p->llr + (size_t)slot * c->N * c->m, p->h_llr + (size_t)slot * c->N * c->m,
-                      r.llr.size() * 4, cudaMemcpyHostToDevice, s);
+      memcpy(p->h_llr + (size_t)i * per, r.llr.data(), per * 4);
       p->h_io[i] = slot;
-      p->h_maxit[slot] = r.max_iter;
-      cudaMemcpyAsync(p->maxit + slot, p->h_maxit + slot, 4, cudaMemcpyHostToDevice, s);
+      p->h_maxit[i] = r.max_iter;
       p->in_flight[slot] = std::move(r);
     }
-    // new slots appended to the active list, their iteration counters cleared
-    cudaMemcpyAsync(cur + p->active, p->h_io, (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->stage_llr, p->h_llr, (size_t)n_new * per * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->stage_slot, p->h_io, (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->stage_maxit, p->h_maxit, (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
+    const int g = n_new < sm_count() * 8 ? n_new : sm_count() * 8;
+    k_admit<<<g, 128, 0, s>>>(p->stage_llr, p->stage_slot, p->stage_maxit, n_new,
+                              static_cast<int>(per), p->llr, p->iter, p->maxit);
+    // new slots appended to the active list
+    cudaMemcpyAsync(cur + p->active, p->stage_slot, (size_t)n_new * 4, cudaMemcpyDeviceToDevice, s);
     p->h_small[0] = p->active + n_new;
     p->h_small[1] = n_new;
     cudaMemcpyAsync(p->cnt + p->cur, &p->h_small[0], 4, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->cnt + 3, &p->h_small[1], 4, cudaMemcpyHostToDevice, s);
     launch_init_slots(c, p->llr, p->v2c, cur + p->active, p->cnt + 3, n_new, s);
-    // zero the iteration counters of the new slots
-    for (int i = 0; i < n_new; ++i) cudaMemsetAsync(p->iter + p->h_io[i], 0, 4, s);
   }
   const int total = p->active + n_new;
   if (total == 0) return n_new;
@@ -343,10 +406,14 @@ int round_issue(nbfd_server *srv, Pool *p, std::deque<Request> &admit) {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->error = check_cuda(e, "serving kernels");
   }
+  {
+    const int g = total < sm_count() * 8 ? total : sm_count() * 8;
+    k_gather_done<<<g, 128, 0, s>>>(p->done_list, p->cnt + 2, p->sym, p->ok, p->iter, c->N,
+                                    p->pack_sym, p->pack_ok, p->pack_iter);
+  }
   // counts back: [active next, done]
   cudaMemcpyAsync(&p->h_small[2], p->cnt + (p->cur ^ 1), 4, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&p->h_small[3], p->cnt + 2, 4, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(p->h_io, p->done_list, (size_t)total * 4, cudaMemcpyDeviceToHost, s);
   return n_new;
 }
 
@@ -384,24 +451,23 @@ void worker_main(nbfd_server *srv) {
       cudaStreamSynchronize(p->stream);
       const int n_next = p->h_small[2], n_done = p->h_small[3];
       const nbfd_code *c = p->code;
-      std::vector<int> done(p->h_io, p->h_io + n_done);
-      for (int i = 0; i < n_done; ++i) {
-        const int slot = done[i];
-        cudaMemcpyAsync(p->h_sym + (size_t)slot * c->N, p->sym + (size_t)slot * c->N,
-                        (size_t)c->N * 2, cudaMemcpyDeviceToHost, p->stream);
-        cudaMemcpyAsync(p->h_ok + slot, p->ok + slot, 1, cudaMemcpyDeviceToHost, p->stream);
-        cudaMemcpyAsync(p->h_iters + slot, p->iter + slot, 4, cudaMemcpyDeviceToHost, p->stream);
+      if (n_done) {
+        cudaMemcpyAsync(p->h_io, p->done_list, (size_t)n_done * 4, cudaMemcpyDeviceToHost, p->stream);
+        cudaMemcpyAsync(p->h_sym, p->pack_sym, (size_t)n_done * c->N * 2, cudaMemcpyDeviceToHost, p->stream);
+        cudaMemcpyAsync(p->h_ok, p->pack_ok, (size_t)n_done, cudaMemcpyDeviceToHost, p->stream);
+        cudaMemcpyAsync(p->h_iters, p->pack_iter, (size_t)n_done * 4, cudaMemcpyDeviceToHost, p->stream);
+        cudaStreamSynchronize(p->stream);
       }
-      if (n_done) cudaStreamSynchronize(p->stream);
       const double t = now_s();
       std::lock_guard<std::mutex> lk(srv->mu);
-      for (int slot : done) {
+      for (int i = 0; i < n_done; ++i) {
+        const int slot = p->h_io[i];
         auto it = p->in_flight.find(slot);
         if (it == p->in_flight.end()) continue;
         Result r;
-        r.sym.assign(p->h_sym + (size_t)slot * c->N, p->h_sym + (size_t)slot * c->N + c->N);
-        r.ok = p->h_ok[slot];
-        r.iters = p->h_iters[slot];
+        r.sym.assign(p->h_sym + (size_t)i * c->N, p->h_sym + (size_t)i * c->N + c->N);
+        r.ok = p->h_ok[i];
+        r.iters = p->h_iters[i];
         r.latency = t - it->second.t_submit;
         srv->done[it->second.ticket] = std::move(r);
         srv->done_order.push_back(it->second.ticket);
