@@ -26,13 +26,15 @@ __device__ __forceinline__ float gamma_decode(float g) {
   return __uint_as_float(__float_as_uint(e) | (__float_as_uint(g) & 0x80000000u));
 }
 
+// A length-Q vector held by a group of LPV lanes, VPT consecutive entries per lane (up to 8 in
+// registers, so that at most log2(Q) - 3 butterfly stages cross lanes).
 template <int MB>
 struct ChannelLayout {
   static constexpr int Q = 1 << MB;
-  static constexpr int VPT = Q >= 32 ? Q / 32 : 1;  // values per lane
+  static constexpr int VPT = Q >= 8 ? 8 : Q;        // values per lane
   static constexpr int LPV = Q / VPT;               // lanes per vector (a power of two <= 32)
   static constexpr int VPW = 32 / LPV;              // vectors per warp
-  static constexpr int LOG_VPT = MB - (Q >= 32 ? 5 : MB);
+  static constexpr int LOG_VPT = MB >= 3 ? 3 : MB;
 };
 
 // p0(x) = prod_i Pr(b_i = x_i | L_i) for one variable, at x = l*VPT + j in P[j] (lane l of a
@@ -111,6 +113,10 @@ template <int MB>
 __device__ __forceinline__ void channel_probs_shared(const float *__restrict__ L, int l,
                                                      float (&P)[ChannelLayout<MB>::VPT]) {
   using CL = ChannelLayout<MB>;
+  if constexpr (CL::LPV < MB) {  // fewer lanes than bits: each lane computes its own
+    channel_probs<MB>(L, l, P);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int base = lane - l;
   float my0 = 1.0f, my1 = 0.0f;

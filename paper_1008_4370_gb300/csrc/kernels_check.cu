@@ -181,27 +181,168 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Per-warp variant: each warp runs its own S-stage pipeline of tiles of CPW checks (no block
+// barriers); lane l works on entries t = l*EPL .. l*EPL+EPL-1 of the tile (check t / Q, z = t % Q,
+// EPL consecutive z of one check), so the index map of an edge is read as EPL consecutive bytes.
+template <int MB, int KMAX>
+struct WarpCheck {
+  static constexpr int Q = 1 << MB;
+  static constexpr int EPL = Q < 8 ? Q : 8;  // entries per lane
+  static constexpr int CPW = 32 * EPL / Q;   // checks per warp tile
+};
+
+template <int MB, int KMAX>
+__global__ void __launch_bounds__(256)
+    k_check_warp(const float *__restrict__ v2c, float *__restrict__ c2v,
+                 const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
+                 int E, int S, FrameSet fs, int32_t *err) {
+  using WC = WarpCheck<MB, KMAX>;
+  constexpr int Q = WC::Q, EPL = WC::EPL, CPW = WC::CPW;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + wib * 8;
+  const size_t tile_floats = (size_t)CPW * k * Q;
+  float *stages = reinterpret_cast<float *>(smem_raw + 128 * 8) + (size_t)wib * S * tile_floats;
+  const long long total = (long long)n_frames_of(fs) * M;
+  const long long n_tiles = (total + CPW - 1) / CPW;
+  const long long gw = (long long)blockIdx.x * nwarps + wib;
+  const long long nw = (long long)gridDim.x * nwarps;
+  const long long my_count = gw < n_tiles ? (n_tiles - gw + nw - 1) / nw : 0;
+  if (my_count == 0) return;
+  if (lane == 0) {
+    for (int b = 0; b < S; ++b) mbar_init(&bars[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  long long issued = 0;
+  auto issue = [&](long long j) {
+    const long long tj = gw + j * nw;
+    const int bj = static_cast<int>(j % S);
+    const long long first = tj * CPW;
+    const long long n = (first + CPW < total ? CPW : total - first);
+    mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n) * k * Q * 4u);
+    stage_copies<true>(fs, tj, CPW, total, M, k, E, Q, v2c, nullptr,
+                       stages + (size_t)bj * tile_floats, &bars[bj]);
+  };
+  if (lane == 0)
+    for (; issued < S - 2 && issued < my_count; ++issued) issue(issued);
+  const int ci = lane * EPL / Q;       // this lane's check within the tile
+  const int z0 = (lane * EPL) % Q;     // first of its EPL entries
+  long long i = 0;
+  bool failed = false;
+  for (; i < my_count; ++i) {
+    const int b = static_cast<int>(i % S);
+    const long long tile = gw + i * nw;
+    if (lane == 0 && issued < my_count) {
+      bulk_wait_read_all_but_one();  // the buffer of tile i-2 was written back
+      issue(issued);
+      ++issued;
+    }
+    const bool ok = mbar_wait_bounded(&bars[b], static_cast<uint32_t>((i / S) & 1));
+    if (__any_sync(0xffffffffu, !ok)) {
+      failed = true;
+      break;
+    }
+    const long long item = tile * CPW + ci;
+    if (item < total) {
+      const int c = static_cast<int>(item % M);
+      float *s = stages + (size_t)b * tile_floats + (size_t)ci * k * Q;
+      // index maps of the k edges at this lane's EPL entries
+      uint32_t pw[KMAX][(EPL + 3) / 4];
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) {
+        if (e < k) {
+          const int h = __ldg(edge_h + (size_t)c * k + e);
+          const uint8_t *row = perm + h * Q + z0;
+          if constexpr (EPL == 8) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row));
+            pw[e][0] = w.x;
+            pw[e][1] = w.y;
+          } else if constexpr (EPL == 4) {
+            pw[e][0] = __ldg(reinterpret_cast<const uint32_t *>(row));
+          } else {
+            uint32_t w = 0;
+#pragma unroll
+            for (int jj = 0; jj < EPL; ++jj) w |= (uint32_t)__ldg(row + jj) << (8 * jj);
+            pw[e][0] = w;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < EPL; ++j) {
+        float mag[KMAX];
+        uint32_t sg[KMAX];
+        int pos[KMAX];
+        uint32_t sx = 0;
+#pragma unroll
+        for (int e = 0; e < KMAX; ++e) {
+          if (e < k) {
+            pos[e] = (pw[e][j >> 2] >> (8 * (j & 3))) & 0xff;
+            const float x = s[e * Q + pos[e]];
+            mag[e] = fabsf(x);
+            sg[e] = __float_as_uint(x) & 0x80000000u;
+            sx ^= sg[e];
+          }
+        }
+        float suf[KMAX];
+        float run = 0.0f;
+#pragma unroll
+        for (int e = KMAX - 1; e >= 0; --e) {
+          if (e < k) {
+            suf[e] = run;
+            run += mag[e];
+          }
+        }
+        float pre = 0.0f;
+#pragma unroll
+        for (int e = 0; e < KMAX; ++e) {
+          if (e < k) {
+            const float o = pre + suf[e];
+            pre += mag[e];
+            s[e * Q + pos[e]] = __uint_as_float(__float_as_uint(o) | (sx ^ sg[e]));
+          }
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      stage_copies<false>(fs, tile, CPW, total, M, k, E, Q, nullptr, c2v,
+                          stages + (size_t)b * tile_floats, nullptr);
+      bulk_commit();
+    }
+  }
+  if (lane == 0) {
+    if (failed) {
+      if (err) atomicExch(err, NBFD_ETIMEDOUT);
+      for (long long j = i; j < issued; ++j)
+        mbar_wait_bounded(&bars[j % S], static_cast<uint32_t>((j / S) & 1));
+    }
+    bulk_wait_all();
+  }
+}
+
 cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
                               int32_t *err, cudaStream_t s) {
   const int Q = c->q, k = c->k;
-  const int ipb = 256 / Q;
-  // about 16 KiB of checks per stage, a multiple of the 256/Q checks one pass of threads covers
-  int g = (16 * 1024) / (ipb * k * Q * 4);
-  if (g < 1) g = 1;
-  const int T = ipb * g;
-  const int S = (size_t)T * k * Q * 4 > 24 * 1024 ? 4 : 5;
-  const size_t smem = 128 + (size_t)S * T * k * Q * 4;
+  const int epl = Q < 8 ? Q : 8;
+  const int cpw = 32 * epl / Q;
+  const int S = 3;
+  const int warps = k <= 4 ? 8 : (k <= 8 ? 4 : (k <= 16 ? 2 : 1));
+  const size_t smem = 128 * 8 + (size_t)warps * S * cpw * k * Q * 4;
   const long long total = (long long)fs.n_static * c->M;
-  const long long n_stages = (total + T - 1) / T;
-  long long grid = (long long)sm_count() * (smem <= 56 * 1024 ? 3 : 2);
-  if (grid > n_stages) grid = n_stages;
+  const long long n_tiles = (total + cpw - 1) / cpw;
+  long long grid = (long long)sm_count() * 2;
+  const long long need = (n_tiles + warps - 1) / warps;
+  if (grid > need) grid = need;
   if (grid < 1) grid = 1;
 #define NBFD_CHK(MB, KM)                                                                      \
   {                                                                                           \
-    cudaFuncSetAttribute(k_check_bulk<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+    cudaFuncSetAttribute(k_check_warp<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                          (int)smem);                                                          \
-    k_check_bulk<MB, KM><<<(int)grid, 256, smem, s>>>(v2c, c2v, c->d_edge_h, c->d_perm, c->M,  \
-                                                       k, c->E, T, S, fs, err);               \
+    k_check_warp<MB, KM><<<(int)grid, warps * 32, smem, s>>>(v2c, c2v, c->d_edge_h, c->d_perm, \
+                                                              c->M, k, c->E, S, fs, err);     \
   }
 #define NBFD_CHK_M(MB)                     \
   {                                        \

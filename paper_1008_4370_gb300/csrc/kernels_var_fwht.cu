@@ -106,6 +106,12 @@ __device__ __forceinline__ void var_issue(VarStage<MB> &ws, int st, long long ba
   }
 }
 
+// warps per block: 8 unless the per-warp stages would pass the 48 KiB static shared-memory limit
+template <int MB>
+constexpr int fwht_wpb() {
+  return sizeof(VarStage<MB>) * 8 <= 46 * 1024 ? 8 : 4;
+}
+
 template <int MB>
 __global__ void __launch_bounds__(256, 3)
     k_var_fwht(const float *__restrict__ llr, const float *__restrict__ c2v,
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(256, 3)
                const uint8_t *__restrict__ perm, int N, int E, FrameSet fs, int32_t *err) {
   using CL = ChannelLayout<MB>;
   constexpr int Q = CL::Q, VPT = CL::VPT, LPV = CL::LPV, VPW = CL::VPW;
-  __shared__ VarStage<MB> stage_mem[8];
+  __shared__ VarStage<MB> stage_mem[fwht_wpb<MB>()];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   VarStage<MB> &ws = stage_mem[wib];
   const int sub = lane / LPV, l = lane % LPV;
@@ -242,11 +248,11 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
   const long long cap = (long long)sm_count() * 8;
 #define NBFD_VAR_FWHT(MB)                                                                   \
   {                                                                                         \
-    constexpr int VPW = ChannelLayout<MB>::VPW;                                             \
-    long long g = (total + 8 * VPW - 1) / (8 * VPW);                                        \
-    if (g > cap) g = cap;                                                                   \
+    constexpr int VPW = ChannelLayout<MB>::VPW, WPB = fwht_wpb<MB>();                       \
+    long long g = (total + WPB * VPW - 1) / (WPB * VPW);                                    \
+    if (g > cap * 8 / WPB) g = cap * 8 / WPB;                                               \
     if (g < 1) g = 1;                                                                       \
-    k_var_fwht<MB><<<(int)g, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,         \
+    k_var_fwht<MB><<<(int)g, 32 * WPB, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,         \
                                           c->d_edge_h, c->d_perm, c->N, c->E, fs, err);     \
   }
   switch (c->m) {
