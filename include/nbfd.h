@@ -259,8 +259,11 @@ void nbfd_srv_destroy(nbfd_server *srv);
 #define NBFD_KERNEL_SYNDROME 3
 #define NBFD_KERNEL_COUNT 4
 
-/* Enable (1) or disable (0) the timers for the calling process; resets the totals. */
-int nbfd_prof_enable(int on);
+/* Time the kernels whose bit (1 << NBFD_KERNEL_*) is set in kernel_mask (0 disables; NBFD_PROF_ALL
+ * times all four) for the calling process; resets the totals. Each timed launch adds two event
+ * records to the stream. */
+#define NBFD_PROF_ALL 0xF
+int nbfd_prof_enable(int kernel_mask);
 /* Totals since the last enable: device milliseconds, launches, and frame-units (the sum over
  * launches of the number of frames the launch processed). Any out pointer may be NULL. */
 int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_units);

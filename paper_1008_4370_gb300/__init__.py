@@ -271,8 +271,9 @@ def nbfd_srv_destroy(srv):
     lib().nbfd_srv_destroy(srv)
 
 
-def nbfd_prof_enable(on: bool):
-    _check(lib().nbfd_prof_enable(1 if on else 0))
+def nbfd_prof_enable(kernel_mask: int):
+    """Time the kernels whose bit (1 << KERNEL_*) is set; 0 disables, 0xF times all."""
+    _check(lib().nbfd_prof_enable(int(kernel_mask)))
 
 
 def nbfd_prof_get(kernel: int):

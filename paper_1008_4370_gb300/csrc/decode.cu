@@ -20,7 +20,7 @@ struct ProfTotals {
   long long units[NBFD_KERNEL_COUNT] = {};
 };
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+int g_prof_mask = 0;  // bit k: time kernel k
 ProfTotals g_prof;
 
 struct PendingTimer {
@@ -35,7 +35,7 @@ std::vector<cudaEvent_t> g_event_pool;  // reused across decodes (guarded by g_p
 
 class Timers {
  public:
-  explicit Timers(bool on) : on_(on) {}
+  explicit Timers(int mask) : on_(mask != 0), mask_(mask) {}
   ~Timers() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto &p : pending_) {
@@ -45,12 +45,13 @@ class Timers {
   }
   bool on() const { return on_; }
   void begin(int kernel, int iter, cudaStream_t s) {
-    if (!on_) return;
+    cur_on_ = on_ && ((mask_ >> kernel) & 1);
+    if (!cur_on_) return;
     cur_ = {kernel, iter, get(), get()};
     cudaEventRecord(cur_.a, s);
   }
   void end(cudaStream_t s) {
-    if (!on_) return;
+    if (!cur_on_) return;
     cudaEventRecord(cur_.b, s);
     pending_.push_back(cur_);
   }
@@ -88,6 +89,8 @@ class Timers {
     return e;
   }
   bool on_;
+  int mask_;
+  bool cur_on_ = false;
   PendingTimer cur_{};
   std::vector<PendingTimer> pending_;
 };
@@ -137,9 +140,9 @@ int check_device(const nbfd_code *c) {
 
 }  // namespace
 
-extern "C" int nbfd_prof_enable(int on) {
+extern "C" int nbfd_prof_enable(int kernel_mask) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  g_prof_on = on != 0;
+  g_prof_mask = kernel_mask & ((1 << NBFD_KERNEL_COUNT) - 1);
   g_prof = ProfTotals{};
   return NBFD_OK;
 }
@@ -184,12 +187,12 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
   Workspace w = carve(c, F, max_iter, static_cast<char *>(workspace));
   int32_t *host_count = nullptr;
   int st = NBFD_OK;
-  bool prof_on;
+  int prof_mask;
   {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    prof_on = g_prof_on;
+    prof_mask = g_prof_mask;
   }
-  Timers tm(prof_on);
+  Timers tm(prof_mask);
   do {
     if ((st = check_cuda(cudaMallocHost(&host_count, sizeof(int32_t)), "cudaMallocHost"))) break;
     if ((st = check_cuda(cudaMemsetAsync(w.count, 0, (size_t)(max_iter + 2) * 4 + 0, s),
