@@ -30,7 +30,7 @@ import numpy as np
 
 from .channel import symbol_probabilities
 from .code import OracleCode
-from .transforms import gamma, logconv, normalize_at_zero, wht
+from .transforms import gamma, gamma_inv, iwht, logconv, normalize_at_zero, wht
 
 _CHUNK_ELEMS = 1 << 22  # bound on the q*q*batch temporaries of the literal log-convolution
 
@@ -141,6 +141,20 @@ def bit_decisions(code: OracleCode, M) -> np.ndarray:
     return x
 
 
+def symbol_decisions(code: OracleCode, M) -> np.ndarray:
+    """x_hat_v = argmax_x mu_v(x), mu_v = inverse transform of M_v (Section 3.2, TENTATIVE
+    DECISION, first form); ties go to the lowest symbol."""
+    mu = iwht(gamma_inv(*M))
+    return np.argmax(mu, axis=-1)
+
+
+def symbol_margin(code: OracleCode, M) -> float:
+    """Smallest (mu(top1) - mu(top2)) / sum |mu| over the variables."""
+    mu = iwht(gamma_inv(*M))
+    srt = np.sort(mu, axis=-1)
+    return float(np.min((srt[:, -1] - srt[:, -2]) / np.abs(mu).sum(axis=-1)))
+
+
 def fourier_syndrome_words(code: OracleCode, M) -> np.ndarray:
     """Per edge (c, v): m-bit word, bit i-1 = sign entry of M_v(H_cv alpha^{i-1}). (E,)"""
     Ms, _ = M
@@ -170,8 +184,14 @@ def decision_margin(code: OracleCode, M) -> float:
     return float(np.exp(worst))
 
 
-def decode(code: OracleCode, llr: np.ndarray, max_iter: int, trace: bool = False):
-    """One frame. Returns dict(symbols, ok, iters, fourier_ok, margins[, trace])."""
+def decode(code: OracleCode, llr: np.ndarray, max_iter: int, trace: bool = False,
+           decision: str = "bitwise"):
+    """One frame. Returns dict(symbols, ok, iters, fourier_ok, margins[, trace]).
+
+    decision="bitwise": the Section 3.2 read-out of M_v(alpha^{i-1}); stop on a zero Fourier-domain
+    syndrome and a zero GF(2^m) syndrome. decision="symbol": x_hat_v = argmax mu_v (the first
+    form of the TENTATIVE DECISION); stop on a zero GF(2^m) syndrome (the Fourier-domain syndrome
+    describes bitwise decisions and is not used)."""
     lam0, v2c = init(code, llr)
     x_hat = None
     ok = False
@@ -183,11 +203,16 @@ def decode(code: OracleCode, llr: np.ndarray, max_iter: int, trace: bool = False
         c2v = check_update(code, v2c)
         v2c = var_update(code, lam0, c2v)
         M = tentative(code, lam0, c2v)
-        x_hat = bit_decisions(code, M)
-        fs = fourier_syndrome(code, M)
+        if decision == "symbol":
+            x_hat = symbol_decisions(code, M)
+            margins.append(symbol_margin(code, M))
+            fok = True
+        else:
+            x_hat = bit_decisions(code, M)
+            fs = fourier_syndrome(code, M)
+            margins.append(decision_margin(code, M))
+            fok = not np.any(fs)
         es = code.syndrome(x_hat)
-        margins.append(decision_margin(code, M))
-        fok = not np.any(fs)
         ok = not np.any(es)
         if trace:
             hist.append({"c2v": c2v, "v2c": v2c, "M": M, "x": x_hat.copy()})

@@ -195,3 +195,43 @@ def test_planted_leave_one_out_error_breaks_sp_equality(monkeypatch):
 
     monkeypatch.setattr(LF, "check_update", include_self)
     assert _max_msg_gap(oc, llr[0], 2) > 1e-3
+
+
+def test_symbol_decisions_equal_sp_argmax():
+    """Section 3.2 first form: argmax of mu_v (inverse transform of M_v) is SP's symbol decision."""
+    code = synth.named_code("gf16_n32_k4")
+    oc = OracleCode.from_dict(code)
+    _, llr = synth.frames(code, 2, 1.0)
+    for f in range(2):
+        p0, v_sp = sp.init(oc, llr[f])
+        lam0, v_lf = LF.init(oc, llr[f])
+        for _ in range(3):
+            c_sp = sp.check_update(oc, v_sp)
+            c_lf = LF.check_update(oc, v_lf)
+            v_sp = sp.var_update(oc, p0, c_sp)
+            v_lf = LF.var_update(oc, lam0, c_lf)
+            qv = sp.marginals(oc, p0, c_sp)
+            x = LF.symbol_decisions(oc, LF.tentative(oc, lam0, c_lf))
+            srt = np.sort(qv, axis=1)
+            clear = (srt[:, -1] - srt[:, -2]) > 1e-9
+            assert np.array_equal(x[clear], np.argmax(qv, axis=1)[clear])
+
+
+def test_symbol_decisions_are_symbol_map_on_trees():
+    code = synth.tree_code(3, 3, 2, seed=3)
+    oc = OracleCode.from_dict(code)
+    cw = BF.codewords(oc)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        llr = rng.normal(0.8, 2.0, size=(oc.N, 2))
+        marg = BF.symbol_marginals(oc, llr, cw)
+        lam0, v = LF.init(oc, llr)
+        for _ in range(8):
+            c = LF.check_update(oc, v)
+            v = LF.var_update(oc, lam0, c)
+        x = LF.symbol_decisions(oc, LF.tentative(oc, lam0, c))
+        srt = np.sort(marg, axis=1)
+        clear = (srt[:, -1] - srt[:, -2]) > 1e-9
+        assert np.array_equal(x[clear], np.argmax(marg, axis=1)[clear])
+        r = LF.decode(oc, llr, 8, decision="symbol")
+        assert r["iters"] >= 1
