@@ -53,6 +53,12 @@ extern "C" {
 #define NBFD_FORM_FP32_TC 4     /* Hadamard transforms on tensor cores, operands split into three
                                    bf16 parts (24 bits) with FP32 accumulate */
 /* The tensor-core forms (1, 2, 4) need m = 8 (q = 256 = 16 x 16); other m give NBFD_ENOTSUP. */
+/* Decision flag, OR'ed into a form: the tentative symbol is argmax_x mu_v(x), the symbol-MAP form
+ * of Section 3.2 (mu_v = inverse transform of M_v, taken directly from the x-domain product),
+ * instead of the bitwise read-out of M_v(alpha^{i-1}); the stop test then uses the GF(2^m)
+ * syndrome alone (the Fourier-domain syndrome describes bitwise decisions). Ties go to the lowest
+ * symbol. Supported with the FWHT and tensor-core forms (not with NBFD_FORM_FP32_DIRECT). */
+#define NBFD_DECIDE_SYMBOL 0x100
 
 typedef struct nbfd_code nbfd_code; /* opaque, library-owned, immutable after creation */
 

@@ -29,6 +29,7 @@ FORM_BF16_HGEMM = 1
 FORM_FP16_HGEMM = 2
 FORM_FP32_FWHT = 3
 FORM_FP32_TC = 4
+DECIDE_SYMBOL = 0x100  # OR into a form: symbol-MAP tentative decisions
 SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT, FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)
 TC_FORMS = (FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)  # need m = 8
 KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME = 0, 1, 2, 3

@@ -362,8 +362,11 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
 }
 
 bool form_supported(int form, int m) {
-  switch (form) {
+  if (form & ~(0xff | NBFD_DECIDE_SYMBOL)) return false;
+  const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
+  switch (form & 0xff) {
     case NBFD_FORM_FP32_DIRECT:
+      return !symbol;  // its M_v is evaluated only at the 3m read-out points
     case NBFD_FORM_FP32_FWHT:
       return true;
     case NBFD_FORM_BF16_HGEMM:
@@ -379,10 +382,12 @@ cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *l
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn,
                        cudaStream_t s, int32_t *err) {
   if (!form_supported(form, c->m)) return cudaErrorNotSupported;
-  if (form == NBFD_FORM_FP32_FWHT)
-    return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s);
-  if (form == NBFD_FORM_BF16_HGEMM || form == NBFD_FORM_FP16_HGEMM || form == NBFD_FORM_FP32_TC)
-    return launch_var_tc(c, fs, form, llr, c2v, v2c, sym, fsyn, err, s);
+  const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
+  const int base = form & 0xff;
+  if (base == NBFD_FORM_FP32_FWHT)
+    return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol);
+  if (base == NBFD_FORM_BF16_HGEMM || base == NBFD_FORM_FP16_HGEMM || base == NBFD_FORM_FP32_TC)
+    return launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol);
   const long long total = (long long)fs.n_static * c->N;
 #define NBFD_VAR(MB)                                                                       \
   {                                                                                        \

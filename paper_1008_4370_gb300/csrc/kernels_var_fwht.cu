@@ -112,7 +112,7 @@ constexpr int fwht_wpb() {
   return sizeof(VarStage<MB>) * 8 <= 46 * 1024 ? 8 : 4;
 }
 
-template <int MB>
+template <int MB, bool SYMBOL>
 __global__ void __launch_bounds__(256, 3)
     k_var_fwht(const float *__restrict__ llr, const float *__restrict__ c2v,
                float *__restrict__ v2c, uint16_t *__restrict__ sym, uint8_t *__restrict__ fsyn,
@@ -173,8 +173,29 @@ __global__ void __launch_bounds__(256, 3)
     channel_probs_shared<MB>(llr + ((size_t)f * N + v) * MB, l, p);  // x-domain channel message
     // M_v = p0 . c1x . c2x (all checks), read out below from shared memory
     float *m_sh = ws.m[sub];
-    float nm;
-    {
+    float nm = 0.0f;
+    int best_x = 0;
+    if constexpr (SYMBOL) {
+      // symbol decision: argmax over x of the x-domain marginal p0 . c1x . c2x (ties: lowest x)
+      float best = -1.0f;
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const float mv = p[j] * c1[j] * c2[j];
+        if (mv > best) {
+          best = mv;
+          best_x = l * VPT + j;
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < LPV; o <<= 1) {
+        const float ob = __shfl_xor_sync(kFull, best, o);
+        const int oi = __shfl_xor_sync(kFull, best_x, o);
+        if (ob > best || (ob == best && oi < best_x)) {
+          best = ob;
+          best_x = oi;
+        }
+      }
+    } else {
       float mm[VPT];
 #pragma unroll
       for (int j = 0; j < VPT; ++j) mm[j] = p[j] * c1[j] * c2[j];
@@ -203,6 +224,19 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
       for (int j = 0; j < VPT; ++j) c1[j] = gamma_encode_fast((l == 0 && j == 0) ? 1.0f : c1[j] * r2);
       st_global<VPT>(v2c + ((size_t)f * E + e2) * Q + l * VPT, c1);
+    }
+    if constexpr (SYMBOL) {
+      // the Fourier-domain syndrome words describe bitwise decisions: with symbol decisions they
+      // are written as 0, so that the stop test rests on the GF(2^m) syndrome alone
+      if (valid && l == 0) {
+        if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(best_x);
+        if (fsyn) {
+          fsyn[(size_t)f * E + e1] = 0;
+          fsyn[(size_t)f * E + e2] = 0;
+        }
+      }
+      __syncwarp();
+      continue;
     }
     // TENTATIVE: signs of M at alpha^{i-1} (t < MB), H_e1 alpha^{i-1} (t < 2MB) and
     // H_e2 alpha^{i-1} (t < 3MB), one read-out point per lane, gathered with ballots.
@@ -243,7 +277,7 @@ __global__ void __launch_bounds__(256, 3)
 
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool symbol) {
   const long long total = (long long)fs.n_static * c->N;
   const long long cap = (long long)sm_count() * 8;
 #define NBFD_VAR_FWHT(MB)                                                                   \
@@ -252,8 +286,14 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
     long long g = (total + WPB * VPW - 1) / (WPB * VPW);                                    \
     if (g > cap * 8 / WPB) g = cap * 8 / WPB;                                               \
     if (g < 1) g = 1;                                                                       \
-    k_var_fwht<MB><<<(int)g, 32 * WPB, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,         \
-                                          c->d_edge_h, c->d_perm, c->N, c->E, fs, err);     \
+    if (symbol)                                                                             \
+      k_var_fwht<MB, true><<<(int)g, 32 * WPB, 0, s>>>(llr, c2v, v2c, sym, fsyn,            \
+                                                       c->d_var_edges, c->d_edge_h,         \
+                                                       c->d_perm, c->N, c->E, fs, err);     \
+    else                                                                                    \
+      k_var_fwht<MB, false><<<(int)g, 32 * WPB, 0, s>>>(llr, c2v, v2c, sym, fsyn,           \
+                                                        c->d_var_edges, c->d_edge_h,        \
+                                                        c->d_perm, c->N, c->E, fs, err);    \
   }
   switch (c->m) {
     case 2: NBFD_VAR_FWHT(2) break;

@@ -226,7 +226,7 @@ __device__ __forceinline__ void tc_issue(TcStage &ws, int st, long long item, lo
 
 }  // namespace
 
-template <int P>
+template <int P, bool SYMBOL>
 __global__ void __launch_bounds__(256, 3)
     k_var_tc(const float *__restrict__ llr, const float *__restrict__ c2v, float *__restrict__ v2c,
              uint16_t *__restrict__ sym, uint8_t *__restrict__ fsyn,
@@ -311,9 +311,31 @@ __global__ void __launch_bounds__(256, 3)
         pr[r] = p;
       }
     }
-    // M_v = p0 . c1x . c2x back to the Fourier domain (natural order), kept for the read-out
-    float nm;
-    {
+    // M_v = p0 . c1x . c2x back to the Fourier domain (natural order), kept for the read-out;
+    // with symbol decisions only its argmax over x (ties: lowest x) is needed
+    float nm = 0.0f;
+    int best_x = 0;
+    if constexpr (SYMBOL) {
+      float best = -1.0f;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float mv = pr[r] * c1[r] * c2[r];
+        const int x = z_transposed(r, g, t);
+        if (mv > best || (mv == best && x < best_x)) {
+          best = mv;
+          best_x = x;
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float ob = __shfl_xor_sync(kFull, best, o);
+        const int oi = __shfl_xor_sync(kFull, best_x, o);
+        if (ob > best || (ob == best && oi < best_x)) {
+          best = ob;
+          best_x = oi;
+        }
+      }
+    } else {
       float mm[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) mm[r] = pr[r] * c1[r] * c2[r];
@@ -346,6 +368,17 @@ __global__ void __launch_bounds__(256, 3)
       *reinterpret_cast<float2 *>(o2 + z_natural(r, g, t)) =
           make_float2(gamma_encode_fast((r == 0 && lane == 0) ? 1.0f : c1[r] * r2),
                       gamma_encode_fast(c1[r + 1] * r2));
+    if constexpr (SYMBOL) {
+      if (lane == 0) {
+        if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(best_x);
+        if (fsyn) {
+          fsyn[(size_t)f * E + e1] = 0;
+          fsyn[(size_t)f * E + e2] = 0;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     // TENTATIVE: signs of M at alpha^{i-1}, H_e1 alpha^{i-1}, H_e2 alpha^{i-1} (lane = point)
     __syncwarp();
     bool neg_pt = false;
@@ -375,29 +408,32 @@ __global__ void __launch_bounds__(256, 3)
 
 cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                           const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool symbol) {
   if (c->m != 8) return cudaErrorNotSupported;
   const long long total = (long long)fs.n_static * c->N;
   long long grid = (total + 7) / 8;
   const long long cap = (long long)sm_count() * 3;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
+#define NBFD_TC(P)                                                                          \
+  {                                                                                         \
+    if (symbol)                                                                             \
+      k_var_tc<P, true><<<(int)grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,  \
+                                                  c->d_edge_h, c->d_perm, c->N, c->E, fs,  \
+                                                  err);                                    \
+    else                                                                                    \
+      k_var_tc<P, false><<<(int)grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges, \
+                                                   c->d_edge_h, c->d_perm, c->N, c->E, fs, \
+                                                   err);                                   \
+  }
   switch (form) {
-    case NBFD_FORM_BF16_HGEMM:
-      k_var_tc<kBF16><<<(int)grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,
-                                                c->d_edge_h, c->d_perm, c->N, c->E, fs, err);
-      break;
-    case NBFD_FORM_FP16_HGEMM:
-      k_var_tc<kFP16><<<(int)grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,
-                                                c->d_edge_h, c->d_perm, c->N, c->E, fs, err);
-      break;
-    case NBFD_FORM_FP32_TC:
-      k_var_tc<kBF16x3><<<(int)grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,
-                                                  c->d_edge_h, c->d_perm, c->N, c->E, fs, err);
-      break;
+    case NBFD_FORM_BF16_HGEMM: NBFD_TC(kBF16) break;
+    case NBFD_FORM_FP16_HGEMM: NBFD_TC(kFP16) break;
+    case NBFD_FORM_FP32_TC: NBFD_TC(kBF16x3) break;
     default:
       return cudaErrorNotSupported;
   }
+#undef NBFD_TC
   return cudaGetLastError();
 }
 

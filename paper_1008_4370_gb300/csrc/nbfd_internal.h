@@ -58,9 +58,9 @@ cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, co
 bool form_supported(int form, int m);
 cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                           const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                          cudaStream_t s);
+                          cudaStream_t s, bool symbol);
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                            cudaStream_t s);
+                            cudaStream_t s, bool symbol);
 
 }  // namespace nbfd

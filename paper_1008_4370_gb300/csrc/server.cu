@@ -491,7 +491,8 @@ using namespace nbfd;
 extern "C" int nbfd_srv_create(size_t mem_budget_bytes, int form, nbfd_server **out) {
   if (!out) return set_error(NBFD_EINVAL, "out is NULL");
   *out = nullptr;
-  if (form < 0 || form > NBFD_FORM_FP32_TC) return set_error(NBFD_EINVAL, "bad form %d", form);
+  if ((form & 0xff) > NBFD_FORM_FP32_TC || (form & ~(0xff | NBFD_DECIDE_SYMBOL)))
+    return set_error(NBFD_EINVAL, "bad form %d", form);
   auto *srv = new (std::nothrow) nbfd_server();
   if (!srv) return set_error(NBFD_ENOMEM, "host allocation failed");
   srv->budget = mem_budget_bytes;

@@ -211,7 +211,8 @@ def test_syndrome_parity(dev):
     assert not ex.cpu().numpy()[0].any()
 
 
-def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5, form=nb.FORM_FP32_DIRECT):
+def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5, form=nb.FORM_FP32_DIRECT,
+                      decision="bitwise"):
     """Whole decodes on both sides. Bit-exact symbols and syndrome flags are required on frames
     the oracle decodes (or runs to max_iter) whose last-iteration margin exceeds MARGIN; equal
     iteration counts on frames whose margin exceeds MARGIN at every iteration. Messages do not
@@ -224,7 +225,7 @@ def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5, form=nb.
     sym, ok, it = sym.cpu().numpy().astype(np.int64), ok.cpu().numpy(), it.cpu().numpy()
     n_sym = n_it = 0
     for f in (range(F) if frames is None else frames):
-        r = LF.decode(oc, llr[f].astype(np.float64), max_iter)
+        r = LF.decode(oc, llr[f].astype(np.float64), max_iter, decision=decision)
         if r["margins"][-1] > MARGIN and (r["ok"] or r["iters"] == max_iter and max_iter <= 4):
             n_sym += 1
             assert np.array_equal(sym[f], r["symbols"]), f
@@ -348,3 +349,37 @@ def test_tc_forms_need_m8(dev):
         with pytest.raises(nb.NbfdError) as ei:
             nb.decode(code, _t(llr, dev), 5, form)
         assert ei.value.status == -10
+
+
+@pytest.mark.parametrize("form", [nb.FORM_FP32_FWHT])
+def test_decode_parity_symbol_decisions_tiny(dev, form):
+    """Symbol-MAP tentative decisions (argmax of mu_v) against the oracle's, GF(16) N=32."""
+    c = synth.named_code("gf16_n32_k4")
+    _, llr = synth.frames(c, 100, 2.0, zero_codeword=True)
+    _decode_vs_oracle(dev, c, llr, 50, min_frac=0.6, form=form | nb.DECIDE_SYMBOL, decision="symbol")
+
+
+@pytest.mark.parametrize("form", [nb.FORM_FP32_FWHT, nb.FORM_FP32_TC])
+def test_decode_parity_symbol_decisions_gf256(dev, form):
+    c = synth.named_code("gf256_n512_k4")
+    tx, llr = synth.frames(c, 256, 1.5)
+    _decode_vs_oracle(dev, c, llr, 4, frames=[0, 99], min_frac=0.5, form=form | nb.DECIDE_SYMBOL,
+                      decision="symbol")
+    code = nb.Code(c)
+    sym, ok, it = nb.decode(code, _t(llr, dev), 100, form | nb.DECIDE_SYMBOL)
+    ex = torch.empty((256, code.M), dtype=torch.int16, device=dev)
+    nb.nbfd_syndrome(code.handle, 256, sym, None, None, ex)
+    torch.cuda.synchronize()
+    ok_h = ok.cpu().numpy().astype(bool)
+    assert np.array_equal(ok_h, ~ex.cpu().numpy().any(axis=1))
+    assert np.mean(np.all(sym.cpu().numpy().astype(np.int64)[ok_h] == tx[ok_h], axis=1)) > 0.99
+    assert ok_h.mean() > 0.9
+
+
+def test_symbol_decisions_not_supported_by_direct_form(dev):
+    c = synth.named_code("gf16_n32_k4")
+    code = nb.Code(c)
+    _, llr = synth.frames(c, 2, 2.0)
+    with pytest.raises(nb.NbfdError) as ei:
+        nb.decode(code, _t(llr, dev), 5, nb.FORM_FP32_DIRECT | nb.DECIDE_SYMBOL)
+    assert ei.value.status == -10
