@@ -180,11 +180,19 @@ extern "C" int nbfd_code_create(int N, int M, int k, int m, uint32_t prim_poly, 
   for (int i = 0; i < 2 * q; ++i) h_exp[i] = static_cast<uint8_t>(gexp[i]);
   for (int x = 1; x < q; ++x) h_log[x] = static_cast<uint8_t>(glog[x]);
 
-  // one device block: [edge_var E*4][var_edges 2N*4][edge_h E][perm q*q][exp 2q][log q]
+  // Fourier-domain syndrome points of every slot: H_cv alpha^i, i < m (Section 3.2)
+  std::vector<uint8_t> h_edge_z(8ull * n_edges, 0);
+  for (int s = 0; s < n_edges; ++s)
+    for (int i = 0; i < m; ++i)
+      h_edge_z[8ull * s + i] = code->index_map[(size_t)h_edge_h[s] * q + (1u << i)];
+
+  // one device block:
+  // [edge_var E*4][var_edges 2N*4][edge_h E][perm q*q][exp 2q][log q][edge_z E*8]
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t off_ev = 0, off_ve = align(off_ev + 4ull * n_edges), off_eh = align(off_ve + 8ull * N),
          off_pm = align(off_eh + n_edges), off_ex = align(off_pm + (size_t)q * q),
-         off_lg = align(off_ex + 2 * q), total = align(off_lg + q);
+         off_lg = align(off_ex + 2 * q), off_ez = align(off_lg + q),
+         total = align(off_ez + 8ull * n_edges);
   cudaError_t err = cudaMalloc(&code->d_block, total);
   if (err != cudaSuccess) {
     delete code;
@@ -197,6 +205,7 @@ extern "C" int nbfd_code_create(int N, int M, int k, int m, uint32_t prim_poly, 
   code->d_perm = reinterpret_cast<uint8_t *>(b + off_pm);
   code->d_gf_exp = reinterpret_cast<uint8_t *>(b + off_ex);
   code->d_gf_log = reinterpret_cast<uint8_t *>(b + off_lg);
+  code->d_edge_z = reinterpret_cast<uint8_t *>(b + off_ez);
   std::vector<char> staging(total, 0);
   memcpy(staging.data() + off_ev, h_edge_var.data(), 4ull * n_edges);
   memcpy(staging.data() + off_ve, h_var_edges.data(), 8ull * N);
@@ -204,6 +213,7 @@ extern "C" int nbfd_code_create(int N, int M, int k, int m, uint32_t prim_poly, 
   memcpy(staging.data() + off_pm, code->index_map.data(), (size_t)q * q);
   memcpy(staging.data() + off_ex, h_exp.data(), 2 * q);
   memcpy(staging.data() + off_lg, h_log.data(), q);
+  memcpy(staging.data() + off_ez, h_edge_z.data(), 8ull * n_edges);
   err = cudaMemcpy(code->d_block, staging.data(), total, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
     cudaFree(code->d_block);

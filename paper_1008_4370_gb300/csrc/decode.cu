@@ -163,6 +163,25 @@ extern "C" size_t nbfd_decode_workspace_size(const nbfd_code *c, int n_frames, i
   return carve(c, n_frames, max_iter, nullptr).bytes;
 }
 
+// A pinned host word per host thread for the active-frame count, allocated on first use and kept
+// for the thread's lifetime (a per-call cudaMallocHost / cudaFreeHost pair would synchronise the
+// device).
+static int32_t *pinned_word() {
+  struct Holder {
+    int32_t *p = nullptr;
+    ~Holder() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  thread_local Holder h;
+  if (!h.p) {
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, 2 * sizeof(int32_t), cudaHostAllocPortable) != cudaSuccess) return nullptr;
+    h.p = static_cast<int32_t *>(p);
+  }
+  return h.p;
+}
+
 extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
                            uint16_t *symbols, uint8_t *ok, int32_t *iters, void *workspace,
                            size_t workspace_bytes, void *stream_) {
@@ -194,7 +213,10 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
   }
   Timers tm(prof_mask);
   do {
-    if ((st = check_cuda(cudaMallocHost(&host_count, sizeof(int32_t)), "cudaMallocHost"))) break;
+    if (!(host_count = pinned_word())) {
+      st = set_error(NBFD_ECUDA, "cudaHostAlloc of the count word failed");
+      break;
+    }
     if ((st = check_cuda(cudaMemsetAsync(w.count, 0, (size_t)(max_iter + 2) * 4 + 0, s),
                          "cudaMemsetAsync")))
       break;
@@ -209,11 +231,13 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
     // The host reads the active-frame count every kSyncEvery iterations; in between it queues
     // iterations blindly (a launch with no active frame returns at once) and sizes each grid by
     // the last count it read, an upper bound since counts only shrink.
-    constexpr int kSyncEvery = 4;
+    // Once few frames are left (the iterations of the frames that do not converge), launches are
+    // short and a host round trip costs as much as several iterations: read the count less often.
     long long active = F;
     int it = 1;
     while (st == NBFD_OK && it <= max_iter && active > 0) {
-      const int last = it + kSyncEvery - 1 < max_iter ? it + kSyncEvery - 1 : max_iter;
+      const int sync_every = active * 16 <= F ? 16 : 4;
+      const int last = it + sync_every - 1 < max_iter ? it + sync_every - 1 : max_iter;
       for (; it <= last; ++it) {
         FrameSet fs;
         fs.list = w.list[it & 1];
@@ -264,7 +288,6 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       tm.flush(counts, F);
     }
   } while (false);
-  if (host_count) cudaFreeHost(host_count);
   if (owned) cudaFreeAsync(workspace, s);
   return st;
 }

@@ -11,6 +11,17 @@ namespace nbfd {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch (sm_90 and later). A kernel launched as a dependent of the
+// previous kernel in its stream may become resident before that kernel ends; griddep_wait()
+// blocks until the previous kernel has completed and its memory operations are visible, so it
+// comes before the first access to anything an earlier kernel wrote. griddep_release() lets the
+// next kernel in the stream start launching (the data it reads is still protected by its own
+// wait). Both are no-ops for a kernel launched normally.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Gamma(r) for |r| <= 1 packed in one float: sign bit = sgn_GF(2)(r) (0 for r == 0),
 // magnitude = -ln|r| (+inf for r == 0). |r| > 1 (a rounding excess over P(0)) clamps to 0.
 __device__ __forceinline__ float gamma_encode(float r) {
@@ -90,6 +101,39 @@ __device__ __forceinline__ void wht_inplace(float (&V)[ChannelLayout<MB>::VPT], 
       V[j] = fmaf(sg, V[j], o);  // exact: a product with +-1 is not rounded
     }
   }
+}
+
+// Single MUFU instructions (PTX ex2/lg2/rcp .approx.ftz): about 2 ulp of relative error; inputs
+// and results below the smallest normal FP32 number are taken as 0.
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2E = 1.4426950408889634f;  // log2(e)
+constexpr float kLn2 = 0.6931471805599453f;     // ln(2)
+
+// Gamma^{-1} as exp(-m) = 2^(-m log2 e) on the ex2 unit
+__device__ __forceinline__ float gamma_decode_ftz(float g) {
+  const float e = ex2_ftz(-fabsf(g) * kLog2E);
+  return __uint_as_float(__float_as_uint(e) | (__float_as_uint(g) & 0x80000000u));
+}
+// Gamma(r) for |r| <= 1 as -ln|r| = -ln 2 * log2|r| on the lg2 unit; r = 0 gives magnitude +inf.
+// A rounding excess |r| = 1 + d gives magnitude |ln|r||, about d (the sign bit of the word must
+// stay the sign of r). r = -0 must not occur (callers add +0 first).
+__device__ __forceinline__ float gamma_encode_ftz(float r) {
+  const float mag = lg2_ftz(fabsf(r)) * -kLn2;
+  return __uint_as_float((__float_as_uint(mag) & 0x7fffffffu) | (__float_as_uint(r) & 0x80000000u));
 }
 
 // Gamma^{-1} with the fast exponential (ex2 unit); a few ulp of relative error per entry.

@@ -286,6 +286,8 @@ __global__ void __launch_bounds__(128)
            int32_t *__restrict__ stats) {
   __shared__ uint8_t gexp[512];
   __shared__ uint8_t glog[256];
+  griddep_wait();
+  griddep_release();
   for (int i = threadIdx.x; i < 2 * q; i += blockDim.x) gexp[i] = gexp_g[i];
   for (int i = threadIdx.x; i < q; i += blockDim.x) glog[i] = glog_g[i];
   __syncthreads();
@@ -414,10 +416,9 @@ cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, co
                         int iter, int max_iter, int32_t *next_list, int32_t *next_count,
                         uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s) {
   const int grid = grid_for(fs.n_static, 16);
-  k_stop<<<grid, 128, 0, s>>>(fs, sym, fsyn, c->d_edge_var, c->d_edge_h, c->d_gf_exp,
-                              c->d_gf_log, c->q, c->N, c->M, c->k, c->E, iter, max_iter,
-                              next_list, next_count, ok, iters, stats);
-  return cudaGetLastError();
+  return launch_dependent(k_stop, dim3(grid), dim3(128), 0, s, fs, sym, fsyn, c->d_edge_var,
+                          c->d_edge_h, c->d_gf_exp, c->d_gf_log, c->q, c->N, c->M, c->k, c->E,
+                          iter, max_iter, next_list, next_count, ok, iters, stats);
 }
 
 }  // namespace nbfd

@@ -198,6 +198,8 @@ __global__ void __launch_bounds__(256)
                  int E, int S, FrameSet fs, int32_t *err) {
   using WC = WarpCheck<MB, KMAX>;
   constexpr int Q = WC::Q, EPL = WC::EPL, CPW = WC::CPW;
+  griddep_wait();
+  griddep_release();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
@@ -341,8 +343,10 @@ cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c,
   {                                                                                           \
     cudaFuncSetAttribute(k_check_warp<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                          (int)smem);                                                          \
-    k_check_warp<MB, KM><<<(int)grid, warps * 32, smem, s>>>(v2c, c2v, c->d_edge_h, c->d_perm, \
-                                                              c->M, k, c->E, S, fs, err);     \
+    const cudaError_t le = launch_dependent(k_check_warp<MB, KM>, dim3((int)grid),             \
+                                            dim3(warps * 32), smem, s, v2c, c2v, c->d_edge_h, \
+                                            c->d_perm, c->M, k, c->E, S, fs, err);            \
+    if (le != cudaSuccess) return le;                                                         \
   }
 #define NBFD_CHK_M(MB)                     \
   {                                        \

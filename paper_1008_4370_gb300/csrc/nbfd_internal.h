@@ -23,6 +23,7 @@ struct nbfd_code {
   uint8_t *d_perm = nullptr;       // [q][q] index map, row h
   uint8_t *d_gf_exp = nullptr;     // [2q] alpha^i, i in [0, 2q)
   uint8_t *d_gf_log = nullptr;     // [q]  log_alpha(x), x != 0
+  uint8_t *d_edge_z = nullptr;     // [E][8] H alpha^i (i < m) of each slot, 0 past m
 };
 
 namespace nbfd {
@@ -37,6 +38,24 @@ struct FrameSet {
 int set_error(int status, const char *fmt, ...);
 int check_cuda(cudaError_t e, const char *what);
 int sm_count();
+
+// Launch with programmatic stream serialization: the kernel may be scheduled while the previous
+// kernel of the stream still runs, and must call griddep_wait() before reading its outputs.
+template <typename... Exp, typename... Act>
+cudaError_t launch_dependent(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Act &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Exp>(args)...);
+}
 
 // kernel launchers (return cudaGetLastError() after the launch)
 cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lambda0, float *v2c,
@@ -62,5 +81,9 @@ cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
                             cudaStream_t s, bool symbol);
+// GF(256) only: the same computation with shared-memory transposes and packed f32x2 butterflies
+cudaError_t launch_var_fwht8(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
+                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
+                             cudaStream_t s, bool symbol);
 
 }  // namespace nbfd
