@@ -37,6 +37,37 @@ CODE_NAME = "gf256_n512_k4"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 
+# DRAM bytes per frame of one launch, from one ncu capture of a 256-frame launch with every frame
+# active (dram__bytes_read.sum + dram__bytes_write.sum, divided by 256), keyed by (kernel, form,
+# code), with the sources the kernel was built from and the first 16 hex digits of the SHA-256 of
+# their concatenation at capture time. A changed source voids the figure (reported as null).
+# Capture: ncu --set full --clock-control none -k regex:<kernel> -s 2 -c 1 python bench.py
+#          --frames 256 --steps 1 --warmup 1 --no-cpu-baseline --serve-requests 0 --plain-steps 0
+#          --batches 1 --form fwht
+MEASURED_TRAFFIC = {
+    ("var", "fwht", "gf256_n512_k4"): {
+        "bytes_per_frame": (272718592 + 219511040) / 256,
+        "sources": ["kernels_var_fwht8.cu", "device_common.cuh", "bulk_copy.cuh"],
+        "sha256_16": "b4f14737a75b3fdd"},
+    ("check", "fwht", "gf256_n512_k4"): {
+        "bytes_per_frame": (268608512 + 214977792) / 256,
+        "sources": ["kernels_check.cu", "device_common.cuh", "bulk_copy.cuh"],
+        "sha256_16": "799a4beb2634e8b1"},
+}
+
+
+def measured_traffic(kernel, form_name, code_name):
+    """Per-frame DRAM bytes of the capture above, or None if absent or its sources changed."""
+    import hashlib
+    rec = MEASURED_TRAFFIC.get((kernel, form_name, code_name))
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_1008_4370_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes_per_frame"] if h.hexdigest()[:16] == rec["sha256_16"] else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -480,8 +511,11 @@ def run_ours(a):
         }[dom]
         achieved = bytes_per_frame * units / (ms / 1e3) / 1e9
         peak = float(peaks["hbm_gbs"])
+        tpf = measured_traffic(names[dom], a.form, CODE_NAME) if a.frames >= 256 else None
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
+                "frac": achieved / peak, "traffic": None if tpf is None else tpf * units / launches,
+                "algorithmic_bytes_per_launch": bytes_per_frame * units / launches,
+                "peak_source": f"{peak_kind} hbm_gbs"}
     timed = {k: prof[k] for k in (1, 2)}
     roof["timed_kernel_ms_share"] = {names[k]: timed[k][0] / max(1e-9, sum(v[0] for v in timed.values()))
                                      for k in timed}
