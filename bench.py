@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--ebn0", type=float, default=1.5)
     ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--batches", type=int, default=4)
+    ap.add_argument("--uneven-steps", type=int, default=3,
+                    help="steps of the uneven five-code batch leg (0: skip)")
     ap.add_argument("--prof-steps", type=int, default=8,
                     help="leading steps of the timed region with per-launch kernel timers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -245,6 +247,64 @@ def reference_mean_iterations():
         with open(p) as f:
             return float(json.load(f)["mean_iterations"])
     return None
+
+
+UNEVEN = [("gf16_n96_k4", 8192), ("gf64_n1200_k6", 2048), ("gf64_n4096_k8", 512),
+          ("gf256_n512_k4", 1024), ("gf256_n2048_k16", 256)]
+
+
+def uneven_leg(nb, torch, dev, form, steps, max_iter):
+    """The uneven-batch configuration (five codes, per-frame Eb/N0 ~ U[1.0, 3.5], max_iter):
+    one nbfd_decode_batch per step (graph-replayed loop, autotuned shapes) against the same
+    frames decoded by one nbfd_decode call per code. Device time per step from CUDA events."""
+    codes, xs, bits, frames = [], [], 0, 0
+    for gi, (name, F) in enumerate(UNEVEN):
+        c = synth.named_code(name)
+        enc = synth.Encoder(c)
+        rng = synth.rng_for(97, gi, 11)
+        _, llr = synth.frames(c, F, rng.uniform(1.0, 3.5, size=F), snr_idx=gi, batch_idx=11, encoder=enc)
+        codes.append(nb.Code(c))
+        xs.append(torch.from_numpy(llr).to(dev))
+        bits += F * enc.info_symbols * c["m"]
+        frames += F
+    handles = [c.handle for c in codes]
+    ns = [int(x.shape[0]) for x in xs]
+    need = nb.nbfd_decode_batch_workspace_size(handles, ns, max_iter, form)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    outs = [(torch.empty((n, c.N), dtype=torch.int16, device=dev), torch.empty(n, dtype=torch.uint8, device=dev),
+             torch.empty(n, dtype=torch.int32, device=dev)) for c, n in zip(codes, ns)]
+    stream = torch.cuda.current_stream()
+
+    def batch(flags=0):
+        nb.nbfd_decode_batch(handles, ns, xs, max_iter, form, flags, [o[0].data_ptr() for o in outs],
+                             [o[1] for o in outs], [o[2] for o in outs], ws, need, stream)
+
+    def per_code():
+        for c, x, n, o in zip(codes, xs, ns, outs):
+            nb.nbfd_decode(c.handle, n, x, max_iter, form, o[0].data_ptr(), o[1], o[2], ws, need, stream)
+
+    batch(nb.BATCH_AUTOTUNE)  # tunes every shape once, then warm
+    batch()
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in (("batch", batch), ("per_code", per_code)):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in ev) / steps
+        res[name] = {"ms_per_step": ms, "mbit_s": bits / (ms / 1e3) / 1e6}
+    oks = [float(o[1].float().mean()) for o in outs]
+    its = [float(o[2].float().mean()) for o in outs]
+    tunes = [nb.nbfd_autotune_result(h, n, form) for h, n in zip(handles, ns)]
+    return {"codes": [n for n, _ in UNEVEN], "frames": ns, "info_bits_per_step": bits,
+            "value": res["batch"]["mbit_s"], "unit": "Mbit/s", "ms_per_step": res["batch"]["ms_per_step"],
+            "per_code_calls": res["per_code"], "steps": steps, "decoded_frac": oks, "mean_iterations": its,
+            "tuned_shapes": [{"check_warps": t[0], "check_stages": t[1], "check_blocks_per_sm": t[2],
+                              "var_blocks_per_sm": t[3]} for t in tunes],
+            "ebn0_db": "per frame U[1.0, 3.5]", "max_iter": max_iter}
 
 
 def serve_run(nb, streams, form, budget, poll_sleep=2e-4, timeout=300.0):
@@ -470,6 +530,9 @@ def run_ours(a):
         plain = {"form": "direct", "value": p_value, "unit": "Mbit/s", "steps": a.plain_steps,
                  "ms_per_step": 1e3 * p_t / a.plain_steps}
     # serving leg: continuous batching of single-frame requests of this code
+    uneven = None
+    if a.uneven_steps > 0 and world == 1 and (form & 0xff) in (FORMS["fwht"], FORMS["direct"]):
+        uneven = uneven_leg(nb, torch, dev, form, a.uneven_steps, a.max_iter)
     served = None
     if a.serve_requests > 0 and world == 1:
         R = a.serve_requests
@@ -554,6 +617,7 @@ def run_ours(a):
         "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": F * N * m * 4,
                 "d2h_bytes_per_step": F * N * 2 + F + F * 4},
         "plain_fp32": plain,
+        "uneven_batch": uneven,
         "served": served,
         "gpu_launches": launches_total,
         "roofline": roof,

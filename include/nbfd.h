@@ -132,6 +132,53 @@ int nbfd_decode(const nbfd_code *code, int n_frames, const float *llr_dev, int m
                 uint16_t *symbols_dev, uint8_t *syndrome_ok_dev, int32_t *iters_dev,
                 void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
+/* ---- uneven batches ------------------------------------------------------------------------
+ * Frames of several codes (different N, k and q) decoded by one call: the same algorithm as
+ * nbfd_decode (Sections 2 and 3.2, the same stop rule and outputs) for every code. The
+ * iteration loop runs as a CUDA graph replayed by the host: one graph holds two iterations of
+ * every code, each code a separate branch, and the loop state (active-frame lists and counts,
+ * iteration number) lives in device memory, so the graph needs no per-iteration arguments.
+ * The host reads the active counts every few replays and stops when no frame is left or
+ * max_iter iterations have run. */
+
+#define NBFD_BATCH_AUTOTUNE 1 /* flags: time launch shapes for shapes not tuned yet (see below) */
+
+/* Device scratch for nbfd_decode_batch (0 on a bad argument). */
+size_t nbfd_decode_batch_workspace_size(int n_codes, const nbfd_code *const *codes,
+                                        const int *n_frames, int max_iter, int form);
+
+/*
+ * nbfd_decode_batch -- decode n_codes groups of frames; group i has n_frames[i] >= 0 frames of
+ * codes[i] (every code on the current device; 1 <= n_codes <= 64).
+ *   llr_dev[i]     : [n_frames[i]][N_i][m_i] float32 bit LLRs (device).
+ *   form           : NBFD_FORM_* (+ NBFD_DECIDE_SYMBOL), supported by every code's field.
+ *   flags          : 0 or NBFD_BATCH_AUTOTUNE.
+ *   symbols_dev[i], syndrome_ok_dev[i], iters_dev[i] : outputs of group i as in nbfd_decode.
+ *   workspace_dev  : >= nbfd_decode_batch_workspace_size() bytes, 256-byte aligned, or NULL
+ *                    (allocated and freed on `cuda_stream`).
+ * Returns after the last iteration's kernels completed. Errors: NBFD_EINVAL, NBFD_ENOTSUP,
+ * NBFD_ENOMEM, NBFD_ECUDA, NBFD_ETIMEDOUT.
+ */
+int nbfd_decode_batch(int n_codes, const nbfd_code *const *codes, const int *n_frames,
+                      const float *const *llr_dev, int max_iter, int form, int flags,
+                      uint16_t *const *symbols_dev, uint8_t *const *syndrome_ok_dev,
+                      int32_t *const *iters_dev, void *workspace_dev, size_t workspace_bytes,
+                      void *cuda_stream);
+
+/*
+ * nbfd_autotune -- time candidate launch shapes of the check kernel (warps per block, bulk-copy
+ * pipeline depth, blocks per SM) and of the variable-node kernel (blocks per SM) for this code,
+ * n_frames and form, on scratch buffers it allocates on `cuda_stream`, and keep the fastest.
+ * Later nbfd_decode / nbfd_decode_batch calls with the same device, code shape (N, k, m),
+ * n_frames and form use it. Synchronises `cuda_stream`. The paper has no counterpart.
+ * Errors: NBFD_EINVAL, NBFD_ENOTSUP, NBFD_ECUDA.
+ */
+int nbfd_autotune(const nbfd_code *code, int n_frames, int form, void *cuda_stream);
+
+/* The shape nbfd_autotune chose (NBFD_EINVAL if this shape was never tuned). */
+int nbfd_autotune_result(const nbfd_code *code, int n_frames, int form, int *check_warps,
+                         int *check_stages, int *check_blocks_per_sm, int *var_blocks_per_sm);
+
 /* ---- decoding without device allocation ----------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers of the library. */
 

@@ -18,6 +18,7 @@ __all__ = [
     "NbfdError", "lib", "FORM_FP32_DIRECT", "FORM_BF16_HGEMM", "FORM_FP16_HGEMM", "FORM_FP32_FWHT", "FORM_FP32_TC",
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
+    "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
     "nbfd_srv_poll", "nbfd_srv_stats", "nbfd_srv_destroy", "nbfd_srv_clock", "nbfd_srv_submit_many",
@@ -50,6 +51,10 @@ SIGNATURES = [
     ("nbfd_decode_workspace_size", ctypes.c_size_t, [_P, _I, _I, _I]),
     ("nbfd_decode", _I, [_P, _I, _P, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     ("nbfd_decode_noalloc", _I, [_P, _I, _P, _I, _I, _P, _P, _P, _P]),
+    ("nbfd_decode_batch_workspace_size", ctypes.c_size_t, [_I, _P, _P, _I, _I]),
+    ("nbfd_decode_batch", _I, [_I, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    ("nbfd_autotune", _I, [_P, _I, _I, _P]),
+    ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P]),
     ("nbfd_init_messages", _I, [_P, _I, _P, _P, _P, _P]),
     ("nbfd_check_update", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_var_update", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
@@ -178,6 +183,47 @@ def nbfd_decode(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, ite
                              _dptr(symbols),
                              _dptr(syndrome_ok, torch.uint8), _dptr(iters, torch.int32),
                              _dptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+BATCH_AUTOTUNE = 1
+
+
+def _ptr_array(ptrs, ctype=ctypes.c_void_p):
+    arr = (ctype * len(ptrs))(*[p if p is not None else 0 for p in ptrs])
+    return arr
+
+
+def nbfd_decode_batch_workspace_size(handles, n_frames, max_iter, form):
+    n = len(handles)
+    return lib().nbfd_decode_batch_workspace_size(n, ctypes.cast(_ptr_array(handles), _P),
+                                                  ctypes.cast((ctypes.c_int * n)(*n_frames), _P),
+                                                  int(max_iter), int(form))
+
+
+def nbfd_decode_batch(handles, n_frames, llrs, max_iter, form, flags, symbols, syndrome_ok, iters,
+                      workspace=None, workspace_bytes=0, stream=None):
+    """One call over several codes: lists (one entry per code) of handles, frame counts, LLR
+    tensors and output tensors."""
+    import torch
+    n = len(handles)
+    _check(lib().nbfd_decode_batch(
+        n, ctypes.cast(_ptr_array(handles), _P), ctypes.cast((ctypes.c_int * n)(*n_frames), _P),
+        ctypes.cast(_ptr_array([_dptr(x, torch.float32) for x in llrs]), _P), int(max_iter), int(form),
+        int(flags), ctypes.cast(_ptr_array([_dptr(x) for x in symbols]), _P),
+        ctypes.cast(_ptr_array([_dptr(x, torch.uint8) for x in syndrome_ok]), _P),
+        ctypes.cast(_ptr_array([_dptr(x, torch.int32) for x in iters]), _P),
+        _dptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def nbfd_autotune(handle, n_frames, form, stream=None):
+    _check(lib().nbfd_autotune(handle, int(n_frames), int(form), _stream(stream)))
+
+
+def nbfd_autotune_result(handle, n_frames, form):
+    """(check warps, check stages, check blocks per SM, variable-node blocks per SM)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().nbfd_autotune_result(handle, int(n_frames), int(form), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def nbfd_decode_noalloc(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, iters, stream=None):
@@ -321,3 +367,19 @@ def decode(code: Code, llr, max_iter: int, form: int = FORM_FP32_DIRECT, workspa
     nbfd_decode(code.handle, F, llr, max_iter, form, sym.data_ptr(), ok, it, workspace, workspace.numel(),
                 stream)
     return sym, ok, it
+
+
+def decode_batch(codes, llrs, max_iter: int, form: int = FORM_FP32_FWHT, flags: int = 0, stream=None):
+    """Allocate outputs and run nbfd_decode_batch over several codes; returns a list of
+    (symbols, ok, iters) per code."""
+    import torch
+    dev = llrs[0].device
+    ns = [int(x.shape[0]) for x in llrs]
+    outs = [(torch.empty((n, c.N), dtype=torch.int16, device=dev), torch.empty(n, dtype=torch.uint8, device=dev),
+             torch.empty(n, dtype=torch.int32, device=dev)) for c, n in zip(codes, ns)]
+    handles = [c.handle for c in codes]
+    need = nbfd_decode_batch_workspace_size(handles, ns, max_iter, form)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    nbfd_decode_batch(handles, ns, llrs, max_iter, form, flags, [o[0].data_ptr() for o in outs],
+                      [o[1] for o in outs], [o[2] for o in outs], ws, ws.numel(), stream)
+    return outs

@@ -212,6 +212,9 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
     prof_mask = g_prof_mask;
   }
   Timers tm(prof_mask);
+  CheckTune check_tune;
+  VarTune var_tune;
+  tune_lookup(c, F, form, &check_tune, &var_tune);  // shapes from nbfd_autotune, if any
   do {
     if (!(host_count = pinned_word())) {
       st = set_error(NBFD_ECUDA, "cudaHostAlloc of the count word failed");
@@ -244,12 +247,13 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
         fs.count = w.count + it;
         fs.n_static = static_cast<int>(active);
         tm.begin(NBFD_KERNEL_CHECK, it, s);
-        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1), "check kernel")))
+        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1, {}, check_tune),
+                             "check kernel")))
           break;
         tm.end(s);
         tm.begin(NBFD_KERNEL_VAR, it, s);
         if ((st = check_cuda(launch_var(c, fs, form, llr, w.c2v, w.v2c, symbols, w.fsyn, s,
-                                        w.stats + 1),
+                                        w.stats + 1, var_tune),
                              "variable kernel")))
           break;
         tm.end(s);

@@ -281,13 +281,15 @@ __global__ void __launch_bounds__(128)
     k_stop(FrameSet fs, const uint16_t *__restrict__ sym, const uint8_t *__restrict__ fsyn,
            const int32_t *__restrict__ edge_var, const uint8_t *__restrict__ edge_h,
            const uint8_t *__restrict__ gexp_g, const uint8_t *__restrict__ glog_g, int q, int N,
-           int M, int k, int E, int iter, int max_iter, int32_t *__restrict__ next_list,
+           int M, int k, int E, int iter_arg, const int32_t *__restrict__ iter_dev, int max_iter,
+           int32_t *__restrict__ next_list,
            int32_t *__restrict__ next_count, uint8_t *__restrict__ ok, int32_t *__restrict__ iters,
            int32_t *__restrict__ stats) {
   __shared__ uint8_t gexp[512];
   __shared__ uint8_t glog[256];
   griddep_wait();
   griddep_release();
+  const int iter = iter_dev ? *iter_dev : iter_arg;
   for (int i = threadIdx.x; i < 2 * q; i += blockDim.x) gexp[i] = gexp_g[i];
   for (int i = threadIdx.x; i < q; i += blockDim.x) glog[i] = glog_g[i];
   __syncthreads();
@@ -358,11 +360,6 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
   return cudaGetLastError();
 }
 
-cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                         cudaStream_t s, int32_t *err) {
-  return launch_check_bulk(c, fs, v2c, c2v, err, s);
-}
-
 bool form_supported(int form, int m) {
   if (form & ~(0xff | NBFD_DECIDE_SYMBOL)) return false;
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
@@ -382,19 +379,20 @@ bool form_supported(int form, int m) {
 
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn,
-                       cudaStream_t s, int32_t *err) {
+                       cudaStream_t s, int32_t *err, VarTune tune) {
   if (!form_supported(form, c->m)) return cudaErrorNotSupported;
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
   const int base = form & 0xff;
   if (base == NBFD_FORM_FP32_FWHT)
-    return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol);
+    return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   if (base == NBFD_FORM_BF16_HGEMM || base == NBFD_FORM_FP16_HGEMM || base == NBFD_FORM_FP32_TC)
-    return launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol);
+    return launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   const long long total = (long long)fs.n_static * c->N;
+  const int per_sm = tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 8;
 #define NBFD_VAR(MB)                                                                       \
   {                                                                                        \
     constexpr int Q = 1 << MB, R = Q < 8 ? Q : 8, VPW = 32 / (Q / R);                      \
-    const int grid = grid_for((total + 8 * VPW - 1) / (8 * VPW), 8);                       \
+    const int grid = grid_for((total + 8 * VPW - 1) / (8 * VPW), per_sm);                  \
     k_var_direct<MB><<<grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,        \
                                           c->d_edge_h, c->d_perm, c->N, c->E, fs);         \
   }
@@ -414,11 +412,12 @@ cudaError_t launch_syndrome(const nbfd_code *c, int F, const uint16_t *sym, cons
 
 cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, const uint8_t *fsyn,
                         int iter, int max_iter, int32_t *next_list, int32_t *next_count,
-                        uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s) {
+                        uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s,
+                        const int32_t *iter_dev) {
   const int grid = grid_for(fs.n_static, 16);
   return launch_dependent(k_stop, dim3(grid), dim3(128), 0, s, fs, sym, fsyn, c->d_edge_var,
                           c->d_edge_h, c->d_gf_exp, c->d_gf_log, c->q, c->N, c->M, c->k, c->E,
-                          iter, max_iter, next_list, next_count, ok, iters, stats);
+                          iter, iter_dev, max_iter, next_list, next_count, ok, iters, stats);
 }
 
 }  // namespace nbfd

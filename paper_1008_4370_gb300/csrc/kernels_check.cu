@@ -1,17 +1,17 @@
-// CHECK TO VARIABLE (Section 3.2) as a bulk-copy pipeline.
+// CHECK TO VARIABLE (Section 3.2) as a per-warp bulk-copy pipeline.
 //
 // A check's k slots are one contiguous block of k*q floats ([slot][z], slots check-major), and
-// consecutive checks of a frame are contiguous too. A block owns a sequence of stages of T
-// checks; thread 0 streams the next S-2 stages into shared memory with cp.async.bulk (the bulk
-// copy engine, completion counted on one mbarrier per stage) while all 256 threads work on the
-// current stage in place: thread (i, z) gathers entry H_e z of every slot e of its check, forms
-// the leave-one-out Gamma sums (prefix and suffix passes: no subtraction, so +inf magnitudes
-// stay exact; signs XOR), and writes output H_e z of slot e back to the same word (z -> H_e z
-// is a bijection, so each word has one reader and one writer). Thread 0 then writes the stage
-// back with one bulk shared->global copy per run of checks of one frame.
+// consecutive checks of a frame are contiguous too. Each warp owns a sequence of tiles of CPW
+// checks; lane 0 streams the next S-2 tiles into the warp's shared memory with cp.async.bulk
+// (the bulk copy engine, completion counted on one mbarrier per stage) while the warp works on
+// the current tile in place: a lane gathers entries H_e z of every slot e of its check, forms the
+// leave-one-out Gamma sums (prefix and suffix passes: no subtraction, so +inf magnitudes stay
+// exact; signs XOR), and writes output H_e z of slot e back to the same word (z -> H_e z is a
+// bijection, so each word has one reader and one writer). Lane 0 then writes the tile back with
+// one bulk shared->global copy per run of checks of one frame.
 //
 // Every mbarrier wait is bounded by a clock budget: on expiry the kernel records
-// NBFD_ETIMEDOUT in *err, waits (bounded) for its own stores and returns.
+// NBFD_ETIMEDOUT in *err, waits (bounded) for its own copies and returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -63,124 +63,6 @@ __device__ uint32_t stage_copies(const FrameSet &fs, long long st, int T, long l
 
 }  // namespace
 
-template <int MB, int KMAX>
-__global__ void __launch_bounds__(256)
-    k_check_bulk(const float *__restrict__ v2c, float *__restrict__ c2v,
-                 const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
-                 int E, int T, int S, FrameSet fs, int32_t *err) {
-  constexpr int Q = 1 << MB;
-  constexpr int IPB = 256 / Q;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
-  float *stages = reinterpret_cast<float *>(smem_raw + 128);
-  const size_t stage_floats = (size_t)T * k * Q;
-  const long long total = (long long)n_frames_of(fs) * M;
-  const long long n_stages = (total + T - 1) / T;
-  const long long my_first = blockIdx.x;
-  const long long my_count =
-      my_first < n_stages ? (n_stages - my_first + gridDim.x - 1) / gridDim.x : 0;
-  if (my_count == 0) return;
-  const int it = threadIdx.x / Q, z = threadIdx.x % Q;
-
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < S; ++b) mbar_init(&bars[b], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  long long issued = 0;  // stages whose loads thread 0 has issued (meaningful in thread 0)
-  if (threadIdx.x == 0) {
-    for (; issued < S - 2 && issued < my_count; ++issued) {
-      const long long st = my_first + issued * gridDim.x;
-      const int bi = static_cast<int>(issued % S);
-      const long long first = st * T;
-      const long long n = (first + T < total ? T : total - first);
-      mbar_expect_tx(&bars[bi], static_cast<uint32_t>(n) * k * Q * 4u);
-      stage_copies<true>(fs, st, T, total, M, k, E, Q, v2c, nullptr,
-                         stages + (size_t)bi * stage_floats, &bars[bi]);
-    }
-  }
-  long long i = 0;
-  bool failed = false;
-  for (; i < my_count; ++i) {
-    const int b = static_cast<int>(i % S);
-    const long long st = my_first + i * gridDim.x;
-    // prefetch stage i+S-2 into the buffer stage i-2 used, once that stage's store has read it
-    // (the store of stage i-1 may still be reading its own buffer)
-    if (threadIdx.x == 0 && issued < my_count) {
-      const long long stj = my_first + issued * gridDim.x;
-      const int bj = static_cast<int>(issued % S);
-      bulk_wait_read_all_but_one();
-      const long long first = stj * T;
-      const long long n = (first + T < total ? T : total - first);
-      mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n) * k * Q * 4u);
-      stage_copies<true>(fs, stj, T, total, M, k, E, Q, v2c, nullptr,
-                         stages + (size_t)bj * stage_floats, &bars[bj]);
-      ++issued;
-    }
-    const bool ok = mbar_wait_bounded(&bars[b], static_cast<uint32_t>((i / S) & 1));
-    if (__syncthreads_or(!ok)) {  // one verdict for the whole block
-      failed = true;
-      break;
-    }
-    float *sbuf = stages + (size_t)b * stage_floats;
-    const long long first = st * T;
-    for (int ci = it; ci < T; ci += IPB) {
-      const long long item = first + ci;
-      if (item >= total) break;
-      const int c = static_cast<int>(item % M);
-      float *s = sbuf + (size_t)ci * k * Q;
-      float mag[KMAX];
-      uint32_t sg[KMAX];
-      int pos[KMAX];
-      uint32_t sx = 0;
-#pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        if (e < k) {
-          const int h = __ldg(edge_h + (size_t)c * k + e);
-          pos[e] = __ldg(perm + h * Q + z);
-          const float x = s[e * Q + pos[e]];
-          mag[e] = fabsf(x);
-          sg[e] = __float_as_uint(x) & 0x80000000u;
-          sx ^= sg[e];
-        }
-      }
-      float suf[KMAX];
-      float run = 0.0f;
-#pragma unroll
-      for (int e = KMAX - 1; e >= 0; --e) {
-        if (e < k) {
-          suf[e] = run;
-          run += mag[e];
-        }
-      }
-      float pre = 0.0f;
-#pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        if (e < k) {
-          const float o = pre + suf[e];
-          pre += mag[e];
-          s[e * Q + pos[e]] = __uint_as_float(__float_as_uint(o) | (sx ^ sg[e]));
-        }
-      }
-    }
-    fence_proxy_async_smem();  // make the in-place results visible to the bulk copy engine
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      stage_copies<false>(fs, st, T, total, M, k, E, Q, nullptr, c2v, sbuf, nullptr);
-      bulk_commit();
-    }
-  }
-  if (threadIdx.x == 0) {
-    if (failed) {
-      if (err) atomicExch(err, NBFD_ETIMEDOUT);
-      // loads still in flight land in this block's shared memory: wait for them (bounded)
-      for (long long j = i; j < issued; ++j)
-        mbar_wait_bounded(&bars[j % S], static_cast<uint32_t>((j / S) & 1));
-    }
-    bulk_wait_all();
-  }
-}
-
 // Per-warp variant: each warp runs its own S-stage pipeline of tiles of CPW checks (no block
 // barriers); lane l works on entries t = l*EPL .. l*EPL+EPL-1 of the tile (check t / Q, z = t % Q,
 // EPL consecutive z of one check), so the index map of an edge is read as EPL consecutive bytes.
@@ -195,11 +77,15 @@ template <int MB, int KMAX>
 __global__ void __launch_bounds__(256)
     k_check_warp(const float *__restrict__ v2c, float *__restrict__ c2v,
                  const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
-                 int E, int S, FrameSet fs, int32_t *err) {
+                 int E, int S, FrameSet fs, int32_t *err, LoopTick tick) {
   using WC = WarpCheck<MB, KMAX>;
   constexpr int Q = WC::Q, EPL = WC::EPL, CPW = WC::CPW;
   griddep_wait();
   griddep_release();
+  if (tick.iter && blockIdx.x == 0 && threadIdx.x == 0) {
+    *tick.iter += 1;   // iteration number of this launch, read by the stop kernel
+    *tick.zero = 0;    // the stop kernel's output count (its previous readers are done)
+  }
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
@@ -325,17 +211,20 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                              int32_t *err, cudaStream_t s) {
+cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
+                         cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune) {
   const int Q = c->q, k = c->k;
   const int epl = Q < 8 ? Q : 8;
   const int cpw = 32 * epl / Q;
-  const int S = 3;
-  const int warps = k <= 4 ? 8 : (k <= 8 ? 4 : (k <= 16 ? 2 : 1));
+  const int S = tune.stages > 0 ? tune.stages : 3;
+  const int warps =
+      tune.warps > 0 ? tune.warps : (k <= 4 ? 8 : (k <= 8 ? 4 : (k <= 16 ? 2 : 1)));
+  const int per_sm = tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 2;
   const size_t smem = 128 * 8 + (size_t)warps * S * cpw * k * Q * 4;
+  if (warps > 8 || S < 3 || smem > kMaxSmemPerBlock) return cudaErrorInvalidValue;
   const long long total = (long long)fs.n_static * c->M;
   const long long n_tiles = (total + cpw - 1) / cpw;
-  long long grid = (long long)sm_count() * 2;
+  long long grid = (long long)sm_count() * per_sm;
   const long long need = (n_tiles + warps - 1) / warps;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
@@ -345,7 +234,7 @@ cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c,
                          (int)smem);                                                          \
     const cudaError_t le = launch_dependent(k_check_warp<MB, KM>, dim3((int)grid),             \
                                             dim3(warps * 32), smem, s, v2c, c2v, c->d_edge_h, \
-                                            c->d_perm, c->M, k, c->E, S, fs, err);            \
+                                            c->d_perm, c->M, k, c->E, S, fs, err, tick);      \
     if (le != cudaSuccess) return le;                                                         \
   }
 #define NBFD_CHK_M(MB)                     \

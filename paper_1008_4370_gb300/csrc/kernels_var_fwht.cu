@@ -277,9 +277,9 @@ __global__ void __launch_bounds__(256, 3)
 
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                            cudaStream_t s, bool symbol) {
+                            cudaStream_t s, bool symbol, VarTune tune) {
   const long long total = (long long)fs.n_static * c->N;
-  const long long cap = (long long)sm_count() * 8;
+  const long long cap = (long long)sm_count() * (tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 8);
 #define NBFD_VAR_FWHT(MB)                                                                   \
   {                                                                                         \
     constexpr int VPW = ChannelLayout<MB>::VPW, WPB = fwht_wpb<MB>();                       \
@@ -302,7 +302,7 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
     case 5: NBFD_VAR_FWHT(5) break;
     case 6: NBFD_VAR_FWHT(6) break;
     case 7: NBFD_VAR_FWHT(7) break;
-    case 8: return launch_var_fwht8(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol);
+    case 8: return launch_var_fwht8(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
     default: return cudaErrorInvalidValue;
   }
 #undef NBFD_VAR_FWHT

@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(32 * kWarps, 3)
 
 cudaError_t launch_var_fwht8(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                              float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                             cudaStream_t s, bool symbol) {
+                             cudaStream_t s, bool symbol, VarTune tune) {
   if (c->m != 8) return cudaErrorInvalidValue;
   auto kern = symbol ? k_var_fwht8<true> : k_var_fwht8<false>;
   const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -430,7 +430,8 @@ cudaError_t launch_var_fwht8(const nbfd_code *c, FrameSet fs, const float *llr, 
   if (e != cudaSuccess) return e;
   const long long total = (long long)fs.n_static * c->N;
   long long g = (total + kWarps - 1) / kWarps;
-  const long long cap = (long long)sm_count() * 3;
+  const int per_sm = tune.blocks_per_sm > 0 && tune.blocks_per_sm < 3 ? tune.blocks_per_sm : 3;
+  const long long cap = (long long)sm_count() * per_sm;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return launch_dependent(kern, dim3((int)g), dim3(32 * kWarps), kSmemBytes, s, llr, c2v, v2c, sym,

@@ -408,11 +408,11 @@ __global__ void __launch_bounds__(256, 3)
 
 cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                           const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                          cudaStream_t s, bool symbol) {
+                          cudaStream_t s, bool symbol, VarTune tune) {
   if (c->m != 8) return cudaErrorNotSupported;
   const long long total = (long long)fs.n_static * c->N;
   long long grid = (total + 7) / 8;
-  const long long cap = (long long)sm_count() * 3;
+  const long long cap = (long long)sm_count() * (tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 3);
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
 #define NBFD_TC(P)                                                                          \

@@ -35,6 +35,27 @@ struct FrameSet {
   int n_static = 0;
 };
 
+// Device words a check-kernel launch updates once (thread 0 of block 0, after the dependent-launch
+// wait), so that a replayed graph of iterations needs no per-iteration arguments: the iteration
+// number *iter is incremented and the next active-frame count *zero is cleared.
+struct LoopTick {
+  int32_t *iter = nullptr;
+  int32_t *zero = nullptr;
+};
+
+// Launch shapes picked by the autotuner (0 = the built-in default).
+struct CheckTune {
+  int warps = 0;          // warps per block, 1..8
+  int stages = 0;         // bulk-copy pipeline depth per warp, 3..8
+  int blocks_per_sm = 0;  // grid cap in blocks per SM
+};
+struct VarTune {
+  int blocks_per_sm = 0;  // grid cap in blocks per SM
+};
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;
+// Launch shapes cached by the autotuner for (device, code shape, n_frames, form), if any.
+bool tune_lookup(const nbfd_code *c, int F, int form, CheckTune *ct, VarTune *vt);
+
 int set_error(int status, const char *fmt, ...);
 int check_cuda(cudaError_t e, const char *what);
 int sm_count();
@@ -62,28 +83,29 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
                         int32_t *list_out, int32_t *count_out, cudaStream_t s);
 // err (device word, may be NULL) receives NBFD_ETIMEDOUT if a bounded wait of the kernel expired.
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                         cudaStream_t s, int32_t *err = nullptr);
-cudaError_t launch_check_bulk(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                              int32_t *err, cudaStream_t s);
+                         cudaStream_t s, int32_t *err = nullptr, LoopTick tick = {},
+                         CheckTune tune = {});
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s,
-                       int32_t *err = nullptr);
+                       int32_t *err = nullptr, VarTune tune = {});
 cudaError_t launch_syndrome(const nbfd_code *c, int F, const uint16_t *sym, const uint8_t *fsyn,
                             uint16_t *fourier, uint16_t *exact, cudaStream_t s);
-// Stop test + compaction of one decoding iteration (see decode.cu).
+// Stop test + compaction of one decoding iteration (see decode.cu). With iter_dev the iteration
+// number is read from that device word instead of `iter`.
 cudaError_t launch_stop(const nbfd_code *c, FrameSet fs, const uint16_t *sym, const uint8_t *fsyn,
                         int iter, int max_iter, int32_t *next_list, int32_t *next_count,
-                        uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s);
+                        uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s,
+                        const int32_t *iter_dev = nullptr);
 bool form_supported(int form, int m);
 cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                           const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                          cudaStream_t s, bool symbol);
+                          cudaStream_t s, bool symbol, VarTune tune = {});
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                            cudaStream_t s, bool symbol);
+                            cudaStream_t s, bool symbol, VarTune tune = {});
 // GF(256) only: the same computation with shared-memory transposes and packed f32x2 butterflies
 cudaError_t launch_var_fwht8(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                              float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                             cudaStream_t s, bool symbol);
+                             cudaStream_t s, bool symbol, VarTune tune = {});
 
 }  // namespace nbfd
