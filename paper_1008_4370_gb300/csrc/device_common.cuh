@@ -189,6 +189,70 @@ __device__ __forceinline__ void channel_probs_shared(const float *__restrict__ L
   }
 }
 
+// INITIALIZATION in closed form: Gamma(P0) of one variable, entry z = l*VPT + j in g[j] (lane l of
+// a group of LPV lanes; `L` points at the MB LLRs of the group's variable). p0 is a product over
+// the m bits, so its transform (Section 2.1) is the product of the bits' own transforms,
+//   P0(z) = prod over the bits i set in z of (Pr(b_i = 0) - Pr(b_i = 1)) = prod tanh(L_i / 2),
+// and Gamma(P0)(z) = (XOR of [L_i < 0], sum of -ln|tanh(L_i / 2)|) over those bits, with
+// -ln|tanh(|L| / 2)| = ln(1 + t) - ln(1 - t), t = exp(-|L|) (+inf at L = 0: P0 vanishes there).
+// P0(0) = 1, so the message is already normalised. The same values as the transform followed by
+// Gamma, with m FP32 additions of non-negative terms per entry instead of exp, butterflies, a
+// division and a logarithm.
+template <int MB>
+__device__ __forceinline__ void channel_gamma(const float *__restrict__ L, int l,
+                                              float (&g)[ChannelLayout<MB>::VPT]) {
+  using CL = ChannelLayout<MB>;
+  float a[MB];
+  uint32_t s[MB];
+  if constexpr (CL::LPV >= MB) {  // lane i < MB of the group computes bit i, shuffles share them
+    const int lane = threadIdx.x & 31;
+    const int base = lane - l;
+    float am = 0.0f;
+    uint32_t sm = 0u;
+    if (l < MB) {
+      const float Li = __ldg(L + l);
+      const float t = expf(-fabsf(Li));
+      am = log1pf(t) - log1pf(-t);
+      sm = Li < 0.0f ? 0x80000000u : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      a[i] = __shfl_sync(kFull, am, base + i);
+      s[i] = __shfl_sync(kFull, sm, base + i);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      const float Li = __ldg(L + i);
+      const float t = expf(-fabsf(Li));
+      a[i] = log1pf(t) - log1pf(-t);
+      s[i] = Li < 0.0f ? 0x80000000u : 0u;
+    }
+  }
+  float A = 0.0f;
+  uint32_t S = 0u;
+#pragma unroll
+  for (int b = CL::LOG_VPT; b < MB; ++b) {
+    if ((l >> (b - CL::LOG_VPT)) & 1) {
+      A += a[b];
+      S ^= s[b];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CL::VPT; ++j) {
+    float mag = A;
+    uint32_t sg = S;
+#pragma unroll
+    for (int b = 0; b < CL::LOG_VPT; ++b) {
+      if ((j >> b) & 1) {
+        mag += a[b];
+        sg ^= s[b];
+      }
+    }
+    g[j] = __uint_as_float(__float_as_uint(mag) | sg);
+  }
+}
+
 // P0(z) = sum_x p0(x) (-1)^{z.x} for one variable (INITIALIZATION of Section 3.2).
 template <int MB>
 __device__ __forceinline__ void channel_fourier(const float *__restrict__ L, int l,

@@ -96,12 +96,8 @@ __global__ void __launch_bounds__(256)
     const long long item = base + sub;
     const bool valid = item < total;
     const long long ic = valid ? item : total - 1;
-    float P[VPT];
-    channel_fourier<MB>(llr + ic * MB, l, P);
-    const float p0 = __shfl_sync(kFull, P[0], sub * CL::LPV);
     float g[VPT];
-#pragma unroll
-    for (int j = 0; j < VPT; ++j) g[j] = gamma_encode(P[j] / p0);
+    channel_gamma<MB>(llr + ic * MB, l, g);
     if (valid) {
       if (lambda0) store_vec<VPT>(lambda0 + item * Q + l * VPT, g);
       if (v2c) {

@@ -56,13 +56,9 @@ __global__ void __launch_bounds__(256)
     const long long ic = valid ? item : total - 1;
     const int f = __ldg(list + ic / N);
     const int v = static_cast<int>(ic % N);
-    float P[VPT];
-    channel_fourier<MB>(llr + ((size_t)f * N + v) * MB, l, P);
-    const float p0 = __shfl_sync(kFull, P[0], sub * CL::LPV);
+    float g[VPT];
+    channel_gamma<MB>(llr + ((size_t)f * N + v) * MB, l, g);
     if (valid) {
-      float g[VPT];
-#pragma unroll
-      for (int j = 0; j < VPT; ++j) g[j] = gamma_encode(P[j] / p0);
       const int e1 = __ldg(var_edges + 2 * v), e2 = __ldg(var_edges + 2 * v + 1);
 #pragma unroll
       for (int j = 0; j < VPT; ++j) {
