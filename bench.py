@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--ebn0", type=float, default=1.5)
     ap.add_argument("--max-iter", type=int, default=100)
     ap.add_argument("--batches", type=int, default=4)
+    ap.add_argument("--store16-steps", type=int, default=10,
+                    help="steps of the half-precision message storage leg (0: skip)")
     ap.add_argument("--uneven-steps", type=int, default=3,
                     help="steps of the uneven five-code batch leg (0: skip)")
     ap.add_argument("--prof-steps", type=int, default=8,
@@ -530,6 +532,32 @@ def run_ours(a):
         plain = {"form": "direct", "value": p_value, "unit": "Mbit/s", "steps": a.plain_steps,
                  "ms_per_step": 1e3 * p_t / a.plain_steps}
     # serving leg: continuous batching of single-frame requests of this code
+    # the same workload with half-precision message storage (FP32 arithmetic): a lower-precision
+    # form of its own, reported beside the FP32 headline
+    store16 = None
+    if a.store16_steps > 0 and form == FORMS["fwht"] and world == 1:
+        f16 = form | nb.STORE_F16
+        need16 = nb.nbfd_decode_workspace_size(code.handle, F, a.max_iter, f16)
+        for i in range(2):
+            nb.nbfd_decode(code.handle, F, batches[i][1], a.max_iter, f16, sym, ok, its, ws, need16, stream)
+        torch.cuda.synchronize()
+        ev16 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(a.store16_steps)]
+        fails16 = 0
+        for i in range(a.store16_steps):
+            ev16[i][0].record(stream)
+            nb.nbfd_decode(code.handle, F, batches[i % len(batches)][1], a.max_iter, f16, sym, ok, its, ws,
+                           need16, stream)
+            ev16[i][1].record(stream)
+            if i < len(batches):
+                torch.cuda.synchronize()
+                fails16 += int((ok == 0).sum().item())
+        torch.cuda.synchronize()
+        ms16 = sum(x.elapsed_time(y) for x, y in ev16) / a.store16_steps
+        store16 = {"form": "fwht + half message storage", "value": info_bits * F / (ms16 / 1e3) / 1e6,
+                   "unit": "Mbit/s", "ms_per_step": ms16, "steps": a.store16_steps,
+                   "fer": fails16 / (F * min(len(batches), a.store16_steps)),
+                   "message_bytes_per_frame_iteration": 4 * E * q * 2 + N * m * 4}
     uneven = None
     if a.uneven_steps > 0 and world == 1 and (form & 0xff) in (FORMS["fwht"], FORMS["direct"]):
         uneven = uneven_leg(nb, torch, dev, form, a.uneven_steps, a.max_iter)
@@ -617,6 +645,7 @@ def run_ours(a):
         "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": F * N * m * 4,
                 "d2h_bytes_per_step": F * N * 2 + F + F * 4},
         "plain_fp32": plain,
+        "store16": store16,
         "uneven_batch": uneven,
         "served": served,
         "gpu_launches": launches_total,

@@ -59,6 +59,14 @@ extern "C" {
  * syndrome alone (the Fourier-domain syndrome describes bitwise decisions). Ties go to the lowest
  * symbol. Supported with the FWHT and tensor-core forms (not with NBFD_FORM_FP32_DIRECT). */
 #define NBFD_DECIDE_SYMBOL 0x100
+/* Storage flag, OR'ed into a form: messages kept in device memory as IEEE half instead of
+ * float -- the same Gamma word (sign bit = GF(2) sign, value = -ln|P|) with its log-magnitude
+ * rounded to an 11-bit significand; all arithmetic stays FP32. Halves the bytes every iteration
+ * moves (the low-precision message storage the paper's log domain allows, Section 3.2). Message
+ * buffers of nbfd_var_update and the *_f16 step calls are then uint16 [frame][slot][z].
+ * Error added per stored entry: |d ln|P|| <= 2^-11 |ln|P||, i.e. |dP| <= 2^-11 / e. Supported
+ * with NBFD_FORM_FP32_FWHT at m = 8 (other combinations give NBFD_ENOTSUP); not by the server. */
+#define NBFD_STORE_F16 0x200
 
 typedef struct nbfd_code nbfd_code; /* opaque, library-owned, immutable after creation */
 
@@ -245,6 +253,14 @@ int nbfd_check_update(const nbfd_code *code, int n_frames, const float *v2c_dev,
 int nbfd_var_update(const nbfd_code *code, int n_frames, int form, const float *llr_dev,
                     const float *c2v_dev, float *v2c_dev, uint16_t *symbols_dev, uint8_t *fsyn_dev,
                     void *cuda_stream);
+
+/* INITIALIZATION and CHECK TO VARIABLE with half-precision message storage (NBFD_STORE_F16):
+ * as nbfd_init_messages (without lambda0) and nbfd_check_update, with uint16 message buffers
+ * [F][E][q] holding IEEE halves. Errors as those calls; NBFD_ENOTSUP unless m = 8. */
+int nbfd_init_messages_f16(const nbfd_code *code, int n_frames, const float *llr_dev,
+                           uint16_t *v2c_dev, void *cuda_stream);
+int nbfd_check_update_f16(const nbfd_code *code, int n_frames, const uint16_t *v2c_dev,
+                          uint16_t *c2v_dev, void *cuda_stream);
 
 /*
  * nbfd_syndrome -- syndromes of Section 3.1/3.2 for every check of every frame:

@@ -107,9 +107,9 @@ struct Workspace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Workspace carve(const nbfd_code *c, int F, int max_iter, char *base) {
+Workspace carve(const nbfd_code *c, int F, int max_iter, int form, char *base) {
   Workspace w{};
-  const size_t msg = align256((size_t)F * c->E * c->q * sizeof(float));
+  const size_t msg = align256((size_t)F * c->E * c->q * (stores_f16(form) ? 2 : 4));
   size_t off = 0;
   w.v2c = reinterpret_cast<float *>(base + off);
   off += msg;
@@ -158,9 +158,8 @@ extern "C" int nbfd_prof_get(int kernel, double *ms, long long *launches, long l
 
 extern "C" size_t nbfd_decode_workspace_size(const nbfd_code *c, int n_frames, int max_iter,
                                              int form) {
-  (void)form;
   if (!c || n_frames < 0 || max_iter < 0) return 0;
-  return carve(c, n_frames, max_iter, nullptr).bytes;
+  return carve(c, n_frames, max_iter, form, nullptr).bytes;
 }
 
 // A pinned host word per host thread for the active-frame count, allocated on first use and kept
@@ -203,7 +202,8 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
     return set_error(NBFD_ENOMEM, "workspace of %zu bytes (need %zu, 256-byte aligned)",
                      workspace_bytes, need);
   }
-  Workspace w = carve(c, F, max_iter, static_cast<char *>(workspace));
+  Workspace w = carve(c, F, max_iter, form, static_cast<char *>(workspace));
+  const bool f16 = stores_f16(form);
   int32_t *host_count = nullptr;
   int st = NBFD_OK;
   int prof_mask;
@@ -227,7 +227,7 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
     if ((st = check_cuda(cudaMemsetAsync(ok, 0, (size_t)F, s), "cudaMemsetAsync"))) break;
     // INITIALIZATION (+ list of iteration 1 = all frames, count[1] = F)
     tm.begin(NBFD_KERNEL_INIT, 0, s);
-    if ((st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s),
+    if ((st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s, f16),
                          "init kernel")))
       break;
     tm.end(s);
@@ -247,7 +247,7 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
         fs.count = w.count + it;
         fs.n_static = static_cast<int>(active);
         tm.begin(NBFD_KERNEL_CHECK, it, s);
-        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1, {}, check_tune),
+        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1, {}, check_tune, f16),
                              "check kernel")))
           break;
         tm.end(s);
@@ -307,6 +307,33 @@ extern "C" int nbfd_init_messages(const nbfd_code *c, int F, const float *llr, f
   return check_cuda(launch_init(c, F, llr, lambda0, v2c, nullptr, nullptr,
                                 static_cast<cudaStream_t>(stream)),
                     "init kernel");
+}
+
+extern "C" int nbfd_init_messages_f16(const nbfd_code *c, int F, const float *llr, uint16_t *v2c,
+                                      void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (c->m != 8) return set_error(NBFD_ENOTSUP, "half message storage needs m = 8");
+  if (F == 0) return NBFD_OK;
+  if (!llr || !v2c) return set_error(NBFD_EINVAL, "NULL buffer");
+  if (int st = check_device(c)) return st;
+  return check_cuda(launch_init(c, F, llr, nullptr, reinterpret_cast<float *>(v2c), nullptr,
+                                nullptr, static_cast<cudaStream_t>(stream), true),
+                    "init kernel");
+}
+
+extern "C" int nbfd_check_update_f16(const nbfd_code *c, int F, const uint16_t *v2c, uint16_t *c2v,
+                                     void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (c->m != 8) return set_error(NBFD_ENOTSUP, "half message storage needs m = 8");
+  if (F == 0) return NBFD_OK;
+  if (!v2c || !c2v || v2c == c2v) return set_error(NBFD_EINVAL, "bad message buffers");
+  if (int st = check_device(c)) return st;
+  FrameSet fs;
+  fs.n_static = F;
+  return check_cuda(launch_check(c, fs, reinterpret_cast<const float *>(v2c),
+                                 reinterpret_cast<float *>(c2v), static_cast<cudaStream_t>(stream),
+                                 nullptr, {}, {}, true),
+                    "check kernel");
 }
 
 extern "C" int nbfd_check_update(const nbfd_code *c, int F, const float *v2c, float *c2v,

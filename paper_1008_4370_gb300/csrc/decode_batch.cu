@@ -86,7 +86,9 @@ int tune_code(const nbfd_code *c, int F, int form, const float *llr, float *v2c,
         // shapes that cannot give every warp a tile are not worth timing twice
         if ((long long)bps * sms * warps > tiles * 2 && bps > 1) continue;
         CheckTune ct{warps, stages, bps};
-        const float ms = time_launches(s, 3, [&] { return launch_check(c, fs, v2c, c2v, s, nullptr, {}, ct); });
+        const float ms = time_launches(s, 3, [&] {
+          return launch_check(c, fs, v2c, c2v, s, nullptr, {}, ct, stores_f16(form));
+        });
         if (ms > 0.0f && (best_ms < 0.0f || ms < best_ms)) {
           best_ms = ms;
           best.check = ct;
@@ -125,10 +127,10 @@ struct CodeWs {
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-CodeWs carve_code(const nbfd_code *c, int F, char *base) {
+CodeWs carve_code(const nbfd_code *c, int F, int form, char *base) {
   CodeWs w{};
   size_t off = 0;
-  const size_t msg = a256((size_t)F * c->E * c->q * sizeof(float));
+  const size_t msg = a256((size_t)F * c->E * c->q * (stores_f16(form) ? 2 : 4));
   w.v2c = reinterpret_cast<float *>(base + off);
   off += msg;
   w.c2v = reinterpret_cast<float *>(base + off);
@@ -202,7 +204,7 @@ extern "C" int nbfd_autotune(const nbfd_code *c, int F, int form, void *stream_)
   if (!form_supported(form, c->m)) return set_error(NBFD_ENOTSUP, "form %d not supported", form);
   if (!code_device_ok(c)) return set_error(NBFD_EINVAL, "current device differs from the code's");
   cudaStream_t s = static_cast<cudaStream_t>(stream_);
-  const size_t msg = a256((size_t)F * c->E * c->q * 4);
+  const size_t msg = a256((size_t)F * c->E * c->q * (stores_f16(form) ? 2 : 4));
   const size_t bytes = 2 * msg + a256((size_t)F * c->N * c->m * 4) + a256((size_t)F * c->N * 2) +
                        a256((size_t)F * c->E);
   char *buf = nullptr;
@@ -214,7 +216,9 @@ extern "C" int nbfd_autotune(const nbfd_code *c, int F, int form, void *stream_)
   uint16_t *sym = reinterpret_cast<uint16_t *>(buf + 2 * msg + a256((size_t)F * c->N * c->m * 4));
   uint8_t *fsyn = reinterpret_cast<uint8_t *>(reinterpret_cast<char *>(sym) + a256((size_t)F * c->N * 2));
   int st = check_cuda(cudaMemsetAsync(llr, 0, (size_t)F * c->N * c->m * 4, s), "cudaMemsetAsync");
-  if (!st) st = check_cuda(launch_init(c, F, llr, nullptr, v2c, nullptr, nullptr, s), "init kernel");
+  if (!st)
+    st = check_cuda(launch_init(c, F, llr, nullptr, v2c, nullptr, nullptr, s, stores_f16(form)),
+                    "init kernel");
   TuneVal tv{};
   if (!st) st = tune_code(c, F, form, llr, v2c, c2v, sym, fsyn, s, &tv);
   cudaFreeAsync(buf, s);
@@ -242,12 +246,11 @@ extern "C" int nbfd_autotune_result(const nbfd_code *c, int F, int form, int *ch
 extern "C" size_t nbfd_decode_batch_workspace_size(int n, const nbfd_code *const *codes,
                                                    const int *n_frames, int max_iter, int form) {
   (void)max_iter;
-  (void)form;
   if (n <= 0 || n > kMaxCodes || !codes || !n_frames) return 0;
   size_t total = 0;
   for (int i = 0; i < n; ++i) {
     if (!codes[i] || n_frames[i] < 0) return 0;
-    total += carve_code(codes[i], n_frames[i], nullptr).bytes;
+    total += carve_code(codes[i], n_frames[i], form, nullptr).bytes;
   }
   return total;
 }
@@ -289,7 +292,7 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
   {
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
-      ws[i] = carve_code(codes[i], n_frames[i], static_cast<char *>(workspace) + off);
+      ws[i] = carve_code(codes[i], n_frames[i], form, static_cast<char *>(workspace) + off);
       off += ws[i].bytes;
     }
   }
@@ -305,7 +308,7 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
     if (!r) r = check_cuda(cudaMemsetAsync(ok[i], 0, (size_t)n_frames[i], s), "cudaMemsetAsync");
     if (!r)
       r = check_cuda(launch_init(c, n_frames[i], llr[i], nullptr, ws[i].v2c, ws[i].list[1],
-                                 ws[i].state + 1, s),
+                                 ws[i].state + 1, s, stores_f16(form)),
                      "init kernel");
     return r;
   };
@@ -363,7 +366,8 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
         LoopTick tick;
         tick.iter = ws[i].state + 2;
         tick.zero = ws[i].state + (1 - p);
-        ce = launch_check(c, fs, ws[i].v2c, ws[i].c2v, b, ws[i].state + 17, tick, tune[i].check);
+        ce = launch_check(c, fs, ws[i].v2c, ws[i].c2v, b, ws[i].state + 17, tick, tune[i].check,
+                          stores_f16(form));
         if (ce == cudaSuccess)
           ce = launch_var(c, fs, form, llr[i], ws[i].c2v, ws[i].v2c, symbols[i], ws[i].fsyn, b,
                           ws[i].state + 17, tune[i].var);

@@ -104,7 +104,8 @@ extern "C" int nbfd_decode_noalloc(const nbfd_code *c, int F, const float *llr, 
     return st;
   if (int st = check_cuda(cudaMemsetAsync(w.stats, 0, 64, s), "cudaMemsetAsync")) return st;
   if (int st = check_cuda(cudaMemsetAsync(ok, 0, (size_t)F, s), "cudaMemsetAsync")) return st;
-  if (int st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s),
+  if (int st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s,
+                                      stores_f16(form)),
                           "init kernel"))
     return st;
   int32_t active = F;  // pageable host word: the copy below completes before it returns
@@ -113,7 +114,9 @@ extern "C" int nbfd_decode_noalloc(const nbfd_code *c, int F, const float *llr, 
     fs.list = w.list[it & 1];
     fs.count = w.count + it;
     fs.n_static = F;
-    if (int st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s), "check kernel")) return st;
+    if (int st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, nullptr, {}, {}, stores_f16(form)),
+                            "check kernel"))
+      return st;
     if (int st = check_cuda(launch_var(c, fs, form, llr, w.c2v, w.v2c, symbols, w.fsyn, s),
                             "variable kernel"))
       return st;

@@ -3,6 +3,7 @@
 // computed with register and warp-shuffle butterflies).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -10,6 +11,40 @@
 namespace nbfd {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Message storage. A Gamma word is a float whose sign bit is the GF(2) sign and whose magnitude
+// is -ln|P|; stored as float (FP32 forms) or rounded to IEEE half (NBFD_STORE_F16: same sign
+// bit, magnitude with an 11-bit significand, +inf kept). Arithmetic is FP32 either way.
+template <typename T>
+__device__ __forceinline__ float msg_load(T x);
+template <>
+__device__ __forceinline__ float msg_load<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float msg_load<__half>(__half x) {
+  return __half2float(x);
+}
+// two Gamma words stored as halves, packed low | high << 16 (lower address first)
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ float2 unpack_half2(uint32_t w) {
+  __half2 h;
+  *reinterpret_cast<uint32_t *>(&h) = w;
+  return __half22float2(h);
+}
+template <typename T>
+__device__ __forceinline__ T msg_store(float x);
+template <>
+__device__ __forceinline__ float msg_store<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ __half msg_store<__half>(float x) {
+  return __float2half_rn(x);
+}
 
 // Programmatic dependent launch (sm_90 and later). A kernel launched as a dependent of the
 // previous kernel in its stream may become resident before that kernel ends; griddep_wait()

@@ -77,9 +77,9 @@ __device__ __forceinline__ int frame_at(const FrameSet &fs, long long slot) {
 // ---------------------------------------------------------------------------------------
 // INITIALIZATION
 // ---------------------------------------------------------------------------------------
-template <int MB>
+template <int MB, typename W>
 __global__ void __launch_bounds__(256)
-    k_init(const float *__restrict__ llr, float *__restrict__ lambda0, float *__restrict__ v2c,
+    k_init(const float *__restrict__ llr, float *__restrict__ lambda0, W *__restrict__ v2c,
            const int32_t *__restrict__ var_edges, int N, int E, int F, int32_t *list_out,
            int32_t *count_out) {
   using CL = ChannelLayout<MB>;
@@ -104,8 +104,19 @@ __global__ void __launch_bounds__(256)
         const long long f = item / N;
         const int v = static_cast<int>(item - f * N);
         const int e1 = __ldg(var_edges + 2 * v), e2 = __ldg(var_edges + 2 * v + 1);
-        store_vec<VPT>(v2c + ((size_t)f * E + e1) * Q + l * VPT, g);
-        store_vec<VPT>(v2c + ((size_t)f * E + e2) * Q + l * VPT, g);
+        if constexpr (sizeof(W) == 4) {
+          store_vec<VPT>(reinterpret_cast<float *>(v2c) + ((size_t)f * E + e1) * Q + l * VPT, g);
+          store_vec<VPT>(reinterpret_cast<float *>(v2c) + ((size_t)f * E + e2) * Q + l * VPT, g);
+        } else {  // 8 halves per lane: one 16-byte store per edge
+          static_assert(VPT == 8, "half storage needs 8 entries per lane");
+          uint4 h;
+          h.x = pack_half2(g[0], g[1]);
+          h.y = pack_half2(g[2], g[3]);
+          h.z = pack_half2(g[4], g[5]);
+          h.w = pack_half2(g[6], g[7]);
+          *reinterpret_cast<uint4 *>(v2c + ((size_t)f * E + e1) * Q + l * VPT) = h;
+          *reinterpret_cast<uint4 *>(v2c + ((size_t)f * E + e2) * Q + l * VPT) = h;
+        }
       }
     }
   }
@@ -342,14 +353,21 @@ static int grid_for(long long work_blocks, int per_sm) {
   }
 
 cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lambda0, float *v2c,
-                        int32_t *list_out, int32_t *count_out, cudaStream_t s) {
+                        int32_t *list_out, int32_t *count_out, cudaStream_t s, bool f16) {
   const long long total = (long long)F * c->N;
+  if (f16) {  // half storage: GF(256) only, no lambda0 output
+    if (c->m != 8 || lambda0) return cudaErrorNotSupported;
+    const int grid = grid_for((total + 7) / 8, 8);
+    k_init<8, __half><<<grid, 256, 0, s>>>(llr, nullptr, reinterpret_cast<__half *>(v2c),
+                                           c->d_var_edges, c->N, c->E, F, list_out, count_out);
+    return cudaGetLastError();
+  }
 #define NBFD_INIT(MB)                                                                        \
   {                                                                                          \
     using CL = ChannelLayout<MB>;                                                            \
     const int grid = grid_for((total + 8 * CL::VPW - 1) / (8 * CL::VPW), 8);                 \
-    k_init<MB><<<grid, 256, 0, s>>>(llr, lambda0, v2c, c->d_var_edges, c->N, c->E, F,        \
-                                    list_out, count_out);                                    \
+    k_init<MB, float><<<grid, 256, 0, s>>>(llr, lambda0, v2c, c->d_var_edges, c->N, c->E, F, \
+                                           list_out, count_out);                             \
   }
   NBFD_DISPATCH_M(c->m, NBFD_INIT)
 #undef NBFD_INIT
@@ -357,8 +375,9 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
 }
 
 bool form_supported(int form, int m) {
-  if (form & ~(0xff | NBFD_DECIDE_SYMBOL)) return false;
+  if (form & ~(0xff | NBFD_DECIDE_SYMBOL | NBFD_STORE_F16)) return false;
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
+  if (stores_f16(form)) return (form & 0xff) == NBFD_FORM_FP32_FWHT && m == 8;
   switch (form & 0xff) {
     case NBFD_FORM_FP32_DIRECT:
       return !symbol;  // its M_v is evaluated only at the 3m read-out points
@@ -380,7 +399,9 @@ cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *l
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
   const int base = form & 0xff;
   if (base == NBFD_FORM_FP32_FWHT)
-    return launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
+    return c->m == 8 ? launch_var_fwht8(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune,
+                                        stores_f16(form))
+                     : launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   if (base == NBFD_FORM_BF16_HGEMM || base == NBFD_FORM_FP16_HGEMM || base == NBFD_FORM_FP32_TC)
     return launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   const long long total = (long long)fs.n_static * c->N;

@@ -33,11 +33,11 @@ __device__ __forceinline__ int frame_id(const FrameSet &fs, long long slot) {
 
 // Issue one bulk copy per run of consecutive checks of one frame in stage `st` (items
 // st*T .. st*T+T-1 of the flattened (frame slot, check) list). Returns the bytes moved.
-template <bool kLoad>
+template <bool kLoad, typename W>
 __device__ uint32_t stage_copies(const FrameSet &fs, long long st, int T, long long total, int M,
-                                 int k, int E, int Q, const float *gsrc, float *gdst, float *sbuf,
+                                 int k, int E, int Q, const W *gsrc, W *gdst, W *sbuf,
                                  uint64_t *bar) {
-  const uint32_t check_bytes = static_cast<uint32_t>(k * Q) * 4u;
+  const uint32_t check_bytes = static_cast<uint32_t>(k * Q * sizeof(W));
   uint32_t bytes = 0;
   long long item = st * T;
   const long long end = (st * T + T < total) ? st * T + T : total;
@@ -48,7 +48,7 @@ __device__ uint32_t stage_copies(const FrameSet &fs, long long st, int T, long l
     if (item + run > end) run = end - item;
     const int f = frame_id(fs, slot);
     const size_t goff = ((size_t)f * E + (size_t)c0 * k) * Q;
-    float *s = sbuf + (size_t)(item - st * T) * k * Q;
+    W *s = sbuf + (size_t)(item - st * T) * k * Q;
     const uint32_t nb = static_cast<uint32_t>(run) * check_bytes;
     if constexpr (kLoad) {
       bulk_load(s, gsrc + goff, nb, bar);
@@ -73,9 +73,9 @@ struct WarpCheck {
   static constexpr int CPW = 32 * EPL / Q;   // checks per warp tile
 };
 
-template <int MB, int KMAX>
+template <int MB, int KMAX, typename W>
 __global__ void __launch_bounds__(256)
-    k_check_warp(const float *__restrict__ v2c, float *__restrict__ c2v,
+    k_check_warp(const W *__restrict__ v2c, W *__restrict__ c2v,
                  const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
                  int E, int S, FrameSet fs, int32_t *err, LoopTick tick) {
   using WC = WarpCheck<MB, KMAX>;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256)
   const int nwarps = blockDim.x >> 5;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + wib * 8;
   const size_t tile_floats = (size_t)CPW * k * Q;
-  float *stages = reinterpret_cast<float *>(smem_raw + 128 * 8) + (size_t)wib * S * tile_floats;
+  W *stages = reinterpret_cast<W *>(smem_raw + 128 * 8) + (size_t)wib * S * tile_floats;
   const long long total = (long long)n_frames_of(fs) * M;
   const long long n_tiles = (total + CPW - 1) / CPW;
   const long long gw = (long long)blockIdx.x * nwarps + wib;
@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256)
     const int bj = static_cast<int>(j % S);
     const long long first = tj * CPW;
     const long long n = (first + CPW < total ? CPW : total - first);
-    mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n) * k * Q * 4u);
-    stage_copies<true>(fs, tj, CPW, total, M, k, E, Q, v2c, nullptr,
+    mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n * k * Q * sizeof(W)));
+    stage_copies<true, W>(fs, tj, CPW, total, M, k, E, Q, v2c, nullptr,
                        stages + (size_t)bj * tile_floats, &bars[bj]);
   };
   if (lane == 0)
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256)
     const long long item = tile * CPW + ci;
     if (item < total) {
       const int c = static_cast<int>(item % M);
-      float *s = stages + (size_t)b * tile_floats + (size_t)ci * k * Q;
+      W *s = stages + (size_t)b * tile_floats + (size_t)ci * k * Q;
       // index maps of the k edges at this lane's EPL entries
       uint32_t pw[KMAX][(EPL + 3) / 4];
 #pragma unroll
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256)
         for (int e = 0; e < KMAX; ++e) {
           if (e < k) {
             pos[e] = (pw[e][j >> 2] >> (8 * (j & 3))) & 0xff;
-            const float x = s[e * Q + pos[e]];
+            const float x = msg_load<W>(s[e * Q + pos[e]]);
             mag[e] = fabsf(x);
             sg[e] = __float_as_uint(x) & 0x80000000u;
             sx ^= sg[e];
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256)
           if (e < k) {
             const float o = pre + suf[e];
             pre += mag[e];
-            s[e * Q + pos[e]] = __uint_as_float(__float_as_uint(o) | (sx ^ sg[e]));
+            s[e * Q + pos[e]] = msg_store<W>(__uint_as_float(__float_as_uint(o) | (sx ^ sg[e])));
           }
         }
       }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256)
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) {
-      stage_copies<false>(fs, tile, CPW, total, M, k, E, Q, nullptr, c2v,
+      stage_copies<false, W>(fs, tile, CPW, total, M, k, E, Q, nullptr, c2v,
                           stages + (size_t)b * tile_floats, nullptr);
       bulk_commit();
     }
@@ -212,37 +212,48 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                         cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune) {
+                         cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune, bool f16) {
   const int Q = c->q, k = c->k;
+  const size_t wb = f16 ? 2 : 4;  // bytes per stored message entry
   const int epl = Q < 8 ? Q : 8;
   const int cpw = 32 * epl / Q;
   const int S = tune.stages > 0 ? tune.stages : 3;
   const int warps =
       tune.warps > 0 ? tune.warps : (k <= 4 ? 8 : (k <= 8 ? 4 : (k <= 16 ? 2 : 1)));
   const int per_sm = tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 2;
-  const size_t smem = 128 * 8 + (size_t)warps * S * cpw * k * Q * 4;
-  if (warps > 8 || S < 3 || smem > kMaxSmemPerBlock) return cudaErrorInvalidValue;
+  const size_t smem = 128 * 8 + (size_t)warps * S * cpw * k * Q * wb;
+  if (warps > 8 || S < 3 || S > 8 || smem > kMaxSmemPerBlock) return cudaErrorInvalidValue;
   const long long total = (long long)fs.n_static * c->M;
   const long long n_tiles = (total + cpw - 1) / cpw;
   long long grid = (long long)sm_count() * per_sm;
   const long long need = (n_tiles + warps - 1) / warps;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-#define NBFD_CHK(MB, KM)                                                                      \
+#define NBFD_CHK_T(MB, KM, W)                                                                \
   {                                                                                           \
-    cudaFuncSetAttribute(k_check_warp<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+    cudaFuncSetAttribute(k_check_warp<MB, KM, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,\
                          (int)smem);                                                          \
-    const cudaError_t le = launch_dependent(k_check_warp<MB, KM>, dim3((int)grid),             \
-                                            dim3(warps * 32), smem, s, v2c, c2v, c->d_edge_h, \
-                                            c->d_perm, c->M, k, c->E, S, fs, err, tick);      \
+    const cudaError_t le = launch_dependent(                                                  \
+        k_check_warp<MB, KM, W>, dim3((int)grid), dim3(warps * 32), smem, s,                  \
+        reinterpret_cast<const W *>(v2c), reinterpret_cast<W *>(c2v), c->d_edge_h, c->d_perm, \
+        c->M, k, c->E, S, fs, err, tick);                                                     \
     if (le != cudaSuccess) return le;                                                         \
   }
+#define NBFD_CHK(MB, KM) NBFD_CHK_T(MB, KM, float)
 #define NBFD_CHK_M(MB)                     \
   {                                        \
     if (k <= 4) NBFD_CHK(MB, 4)            \
     else if (k <= 8) NBFD_CHK(MB, 8)       \
     else if (k <= 16) NBFD_CHK(MB, 16)     \
     else NBFD_CHK(MB, 32)                  \
+  }
+  if (f16) {  // half storage: GF(256) only
+    if (c->m != 8) return cudaErrorNotSupported;
+    if (k <= 4) NBFD_CHK_T(8, 4, __half)
+    else if (k <= 8) NBFD_CHK_T(8, 8, __half)
+    else if (k <= 16) NBFD_CHK_T(8, 16, __half)
+    else NBFD_CHK_T(8, 32, __half)
+    return cudaGetLastError();
   }
   switch (c->m) {
     case 2: NBFD_CHK_M(2) break;
@@ -256,6 +267,7 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
   }
 #undef NBFD_CHK_M
 #undef NBFD_CHK
+#undef NBFD_CHK_T
   return cudaGetLastError();
 }
 

@@ -81,8 +81,9 @@ static_assert(pad_size(kT1Pair) <= 280 && pad_size(kT2Pair) <= 280, "pair scratc
 static_assert(pad_size(kT1One) <= kScratchFloats && pad_size(kT2One) <= kScratchFloats, "scratch");
 
 constexpr int kStages = 3;  // bulk-copy pipeline depth per warp (two variables in flight)
+template <typename W>  // stored message entry: float, or __half with NBFD_STORE_F16
 struct Var8Stage {
-  float msg[kStages][2][kQ];      // [stage][edge 1, edge 2][z], filled by the bulk copy engine
+  W msg[kStages][2][kQ];          // [stage][edge 1, edge 2][z], filled by the bulk copy engine
   float llr[kStages][8];          // [stage][bit] channel LLRs of the variable
   float scratch[kScratchFloats];  // transpose buffer; at the end M in natural order
   int4 idx[kStages];              // [stage] = (frame, variable, slot e1, slot e2)
@@ -90,9 +91,29 @@ struct Var8Stage {
   uint64_t bar[kStages];
   uint64_t pad_;
 };
-static_assert(sizeof(Var8Stage) % 16 == 0, "stage alignment");
+static_assert(sizeof(Var8Stage<float>) % 16 == 0 && sizeof(Var8Stage<__half>) % 16 == 0,
+              "stage alignment");
 constexpr int kWarps = 8;
-constexpr size_t kSmemBytes = sizeof(Var8Stage) * kWarps;
+template <typename W>
+constexpr size_t smem_bytes() {
+  return sizeof(Var8Stage<W>) * kWarps;
+}
+
+// four consecutive stored entries -> floats
+__device__ __forceinline__ float4 load4(const float *p) {
+  return *reinterpret_cast<const float4 *>(p);
+}
+__device__ __forceinline__ float4 load4(const __half *p) {
+  const uint2 w = *reinterpret_cast<const uint2 *>(p);
+  const float2 a = unpack_half2(w.x), b = unpack_half2(w.y);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store4(float *p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(__half *p, float a, float b, float c, float d) {
+  *reinterpret_cast<uint2 *>(p) = make_uint2(pack_half2(a, b), pack_half2(c, d));
+}
 
 __device__ __forceinline__ void bfly(float2 &a, float2 &b) {
   const float2 s = __fadd2_rn(a, b);
@@ -163,15 +184,15 @@ __device__ __forceinline__ void transpose_one(float2 (&u)[4], float *s, uint32_t
 
 }  // namespace
 
-template <bool SYMBOL>
+template <bool SYMBOL, typename W>
 __global__ void __launch_bounds__(32 * kWarps, 3)
-    k_var_fwht8(const float *__restrict__ llr, const float *__restrict__ c2v,
-                float *__restrict__ v2c, uint16_t *__restrict__ sym, uint8_t *__restrict__ fsyn,
+    k_var_fwht8(const float *__restrict__ llr, const W *__restrict__ c2v,
+                W *__restrict__ v2c, uint16_t *__restrict__ sym, uint8_t *__restrict__ fsyn,
                 const int32_t *__restrict__ var_edges, const uint8_t *__restrict__ edge_z,
                 int N, int E, FrameSet fs, int32_t *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Var8Stage &ws = reinterpret_cast<Var8Stage *>(smem_raw)[wib];
+  Var8Stage<W> &ws = reinterpret_cast<Var8Stage<W> *>(smem_raw)[wib];
   griddep_wait();
   griddep_release();
   const int F = fs.list ? __ldg(fs.count) : fs.n_static;
@@ -201,9 +222,10 @@ __global__ void __launch_bounds__(32 * kWarps, 3)
   };
   auto issue = [&](int st) {  // bulk copies of the prefetched item into stage st
     ws.idx[st] = make_int4(pf_f, pf_v, pf_e.x, pf_e.y);
-    mbar_expect_tx(&ws.bar[st], 2u * kQ * 4u + 32u);
-    bulk_load(ws.msg[st][0], c2v + ((size_t)pf_f * E + pf_e.x) * kQ, kQ * 4u, &ws.bar[st]);
-    bulk_load(ws.msg[st][1], c2v + ((size_t)pf_f * E + pf_e.y) * kQ, kQ * 4u, &ws.bar[st]);
+    constexpr uint32_t vb = kQ * sizeof(W);
+    mbar_expect_tx(&ws.bar[st], 2u * vb + 32u);
+    bulk_load(ws.msg[st][0], c2v + ((size_t)pf_f * E + pf_e.x) * kQ, vb, &ws.bar[st]);
+    bulk_load(ws.msg[st][1], c2v + ((size_t)pf_f * E + pf_e.y) * kQ, vb, &ws.bar[st]);
     bulk_load(ws.llr[st], llr + ((size_t)pf_f * N + pf_v) * 8, 32u, &ws.bar[st]);
   };
   if (lane == 0) {
@@ -251,10 +273,10 @@ __global__ void __launch_bounds__(32 * kWarps, 3)
     // both check messages in layout P0, decoded from the Gamma form
     float2 c[8];
     {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&ws.msg[b][0][4 * lane]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&ws.msg[b][0][128 + 4 * lane]);
-      const float4 b0 = *reinterpret_cast<const float4 *>(&ws.msg[b][1][4 * lane]);
-      const float4 b1 = *reinterpret_cast<const float4 *>(&ws.msg[b][1][128 + 4 * lane]);
+      const float4 a0 = load4(&ws.msg[b][0][4 * lane]);
+      const float4 a1 = load4(&ws.msg[b][0][128 + 4 * lane]);
+      const float4 b0 = load4(&ws.msg[b][1][4 * lane]);
+      const float4 b1 = load4(&ws.msg[b][1][128 + 4 * lane]);
       c[0] = make_float2(gamma_decode_ftz(a0.x), gamma_decode_ftz(b0.x));
       c[1] = make_float2(gamma_decode_ftz(a0.y), gamma_decode_ftz(b0.y));
       c[2] = make_float2(gamma_decode_ftz(a0.z), gamma_decode_ftz(b0.z));
@@ -364,11 +386,11 @@ __global__ void __launch_bounds__(32 * kWarps, 3)
       o1[0] = 0.0f;
     }
     {
-      float *d2 = v2c + ((size_t)f * E + e2) * kQ, *d1 = v2c + ((size_t)f * E + e1) * kQ;
-      *reinterpret_cast<float4 *>(d2 + 4 * lane) = make_float4(o2[0], o2[1], o2[2], o2[3]);
-      *reinterpret_cast<float4 *>(d2 + 128 + 4 * lane) = make_float4(o2[4], o2[5], o2[6], o2[7]);
-      *reinterpret_cast<float4 *>(d1 + 4 * lane) = make_float4(o1[0], o1[1], o1[2], o1[3]);
-      *reinterpret_cast<float4 *>(d1 + 128 + 4 * lane) = make_float4(o1[4], o1[5], o1[6], o1[7]);
+      W *d2 = v2c + ((size_t)f * E + e2) * kQ, *d1 = v2c + ((size_t)f * E + e1) * kQ;
+      store4(d2 + 4 * lane, o2[0], o2[1], o2[2], o2[3]);
+      store4(d2 + 128 + 4 * lane, o2[4], o2[5], o2[6], o2[7]);
+      store4(d1 + 4 * lane, o1[0], o1[1], o1[2], o1[3]);
+      store4(d1 + 128 + 4 * lane, o1[4], o1[5], o1[6], o1[7]);
     }
     if constexpr (SYMBOL) {
       // the Fourier-domain syndrome words describe bitwise decisions: with symbol decisions they
@@ -422,20 +444,26 @@ __global__ void __launch_bounds__(32 * kWarps, 3)
 
 cudaError_t launch_var_fwht8(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                              float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                             cudaStream_t s, bool symbol, VarTune tune) {
+                             cudaStream_t s, bool symbol, VarTune tune, bool f16) {
   if (c->m != 8) return cudaErrorInvalidValue;
-  auto kern = symbol ? k_var_fwht8<true> : k_var_fwht8<false>;
-  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kSmemBytes));
-  if (e != cudaSuccess) return e;
   const long long total = (long long)fs.n_static * c->N;
   long long g = (total + kWarps - 1) / kWarps;
   const int per_sm = tune.blocks_per_sm > 0 && tune.blocks_per_sm < 3 ? tune.blocks_per_sm : 3;
   const long long cap = (long long)sm_count() * per_sm;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
-  return launch_dependent(kern, dim3((int)g), dim3(32 * kWarps), kSmemBytes, s, llr, c2v, v2c, sym,
-                          fsyn, c->d_var_edges, c->d_edge_z, c->N, c->E, fs, err);
+  auto go = [&](auto kern, auto tag) -> cudaError_t {
+    using W = decltype(tag);
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem_bytes<W>()));
+    if (e != cudaSuccess) return e;
+    return launch_dependent(kern, dim3((int)g), dim3(32 * kWarps), smem_bytes<W>(), s, llr,
+                            reinterpret_cast<const W *>(c2v), reinterpret_cast<W *>(v2c), sym,
+                            fsyn, c->d_var_edges, c->d_edge_z, c->N, c->E, fs, err);
+  };
+  if (f16)
+    return symbol ? go(k_var_fwht8<true, __half>, __half()) : go(k_var_fwht8<false, __half>, __half());
+  return symbol ? go(k_var_fwht8<true, float>, 0.0f) : go(k_var_fwht8<false, float>, 0.0f);
 }
 
 }  // namespace nbfd

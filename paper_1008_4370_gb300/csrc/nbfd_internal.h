@@ -80,11 +80,13 @@ cudaError_t launch_dependent(void (*kernel)(Exp...), dim3 grid, dim3 block, size
 
 // kernel launchers (return cudaGetLastError() after the launch)
 cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lambda0, float *v2c,
-                        int32_t *list_out, int32_t *count_out, cudaStream_t s);
+                        int32_t *list_out, int32_t *count_out, cudaStream_t s, bool f16 = false);
+inline bool stores_f16(int form) { return (form & NBFD_STORE_F16) != 0; }
 // err (device word, may be NULL) receives NBFD_ETIMEDOUT if a bounded wait of the kernel expired.
+// f16: messages stored as IEEE half (NBFD_STORE_F16); the float pointers then address halves.
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
                          cudaStream_t s, int32_t *err = nullptr, LoopTick tick = {},
-                         CheckTune tune = {});
+                         CheckTune tune = {}, bool f16 = false);
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s,
                        int32_t *err = nullptr, VarTune tune = {});
@@ -106,6 +108,6 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
 // GF(256) only: the same computation with shared-memory transposes and packed f32x2 butterflies
 cudaError_t launch_var_fwht8(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                              float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
-                             cudaStream_t s, bool symbol, VarTune tune = {});
+                             cudaStream_t s, bool symbol, VarTune tune = {}, bool f16 = false);
 
 }  // namespace nbfd

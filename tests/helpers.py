@@ -110,3 +110,42 @@ def vn_margins(oc, M) -> np.ndarray:
         pts = oc.perm[e, [1 << i for i in range(oc.m)]]
         out[v] = min(out[v], np.min(Ml[v, pts] - Ml[v, 0]))
     return np.exp(out)
+
+
+# ---- half-precision message storage (NBFD_STORE_F16) ----------------------------------------
+# A stored Gamma word is the float32 word rounded to IEEE half (round to nearest even): the sign
+# bit is kept and the log-magnitude m = -ln|P| gets an 11-bit significand, so the stored value
+# carries |dm| <= U16 * m, i.e. |dP| = |P| (1 - e^{-dm}) <= U16 * |P| * m <= U16 / e.
+U16 = 2.0 ** -11
+
+
+def to_half(g32: np.ndarray) -> np.ndarray:
+    """Library float32 Gamma words -> the half words the library stores (as float16)."""
+    return np.asarray(g32, dtype=np.float32).astype(np.float16)
+
+
+def compare_store16(gpu16: np.ndarray, s_o: np.ndarray, l_o: np.ndarray, kappa=None):
+    """compare() for half-stored outputs: the FP32 bounds plus the output rounding,
+    linear |dP| <= max(LIN_ATOL, U32 kappa) + U16 |P| |ln|P||, log-magnitude
+    |d ln|P|| <= LOG_ATOL + U16 |ln|P|| on the entries compare() checks; signs where
+    |P| exceeds twice the linear bound."""
+    g = np.asarray(gpu16, dtype=np.float16).astype(np.float32)
+    P_o = gamma_inv(s_o, l_o)
+    P_g = to_linear(g)
+    k = np.ones(P_o.shape[:-1]) if kappa is None else np.asarray(kappa, dtype=np.float64)
+    with np.errstate(invalid="ignore"):
+        store = np.where(np.isfinite(l_o), U16 * np.abs(P_o) * np.abs(l_o), 0.0)
+    tol = np.maximum(LIN_ATOL, U32 * k)[..., None] + store
+    err = np.abs(P_g - P_o)
+    lin_bad = int(np.sum(err > tol * (1 + 1e-9)))
+    well = (U32 * k * 2.0 ** 7 <= LOG_ATOL)[..., None]
+    mask = (np.abs(P_o) >= LOG_FLOOR) & well
+    sg, lg = decode_pair(g)
+    log_bound = LOG_ATOL + U16 * np.abs(l_o)
+    log_bad = int(np.sum(np.abs(lg[mask] - l_o[mask]) > log_bound[mask])) if mask.any() else 0
+    sign_mask = np.abs(P_o) > np.maximum(2 * tol, LOG_FLOOR)
+    sign_bad = int(np.sum(sg[sign_mask] != s_o[sign_mask]))
+    nan = int(np.isnan(g).sum())
+    ok = lin_bad == 0 and log_bad == 0 and sign_bad == 0 and nan == 0
+    return ok, {"lin_max": float(err.max()) if err.size else 0.0, "lin_bad": lin_bad, "log_bad": log_bad,
+                "sign_bad": sign_bad, "nan": nan, "n_log": int(mask.sum())}
