@@ -338,6 +338,14 @@ int nbfd_prof_enable(int kernel_mask);
 int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_units);
 
 /* Message for the calling thread's last failed call ("" if none). */
+/* ---- diagnostics (no counterpart in the paper) ----------------------------------------------
+ * nbfd_diag_wait_expiry -- run the expiry path of the bounded device-side waits on purpose: one
+ * thread waits, with the kernels' bounded mbarrier wait and a budget of budget_cycles SM cycles
+ * (0 .. the kernels' own budget of 4e9), for bulk-copy bytes that are never sent. Nothing is in
+ * flight and nothing faults; the call returns NBFD_ETIMEDOUT (the status nbfd_decode returns when
+ * one of its waits expires) and the CUDA context stays usable. Synchronises `cuda_stream`. */
+int nbfd_diag_wait_expiry(long long budget_cycles, void *cuda_stream);
+
 const char *nbfd_last_error(void);
 /* Static name of a status code. */
 const char *nbfd_status_string(int status);

@@ -36,12 +36,13 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t par
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false when the budget ran out.
-static __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar`; false when `budget` SM cycles ran out.
+static __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                         long long budget = kWaitBudgetCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudgetCycles) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
