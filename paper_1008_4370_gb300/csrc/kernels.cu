@@ -399,8 +399,8 @@ cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *l
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
   const int base = form & 0xff;
   if (base == NBFD_FORM_FP32_FWHT)
-    return c->m == 8 ? launch_var_fwht8(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune,
-                                        stores_f16(form))
+    return c->m == 8 ? launch_var_fwht8x2(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune,
+                                          stores_f16(form))
                      : launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   if (base == NBFD_FORM_BF16_HGEMM || base == NBFD_FORM_FP16_HGEMM || base == NBFD_FORM_FP32_TC)
     return launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);

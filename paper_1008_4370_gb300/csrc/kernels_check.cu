@@ -24,6 +24,12 @@ namespace nbfd {
 
 namespace {
 
+// item / M and item % M; 32-bit when the item count fits (the usual case: F * M < 2^32)
+__device__ __forceinline__ long long div_m(long long item, int M, bool narrow) {
+  return narrow ? static_cast<long long>(static_cast<uint32_t>(item) / static_cast<uint32_t>(M))
+                : item / M;
+}
+
 __device__ __forceinline__ int n_frames_of(const FrameSet &fs) {
   return fs.list ? __ldg(fs.count) : fs.n_static;
 }
@@ -37,12 +43,13 @@ template <bool kLoad, typename W>
 __device__ uint32_t stage_copies(const FrameSet &fs, long long st, int T, long long total, int M,
                                  int k, int E, int Q, const W *gsrc, W *gdst, W *sbuf,
                                  uint64_t *bar) {
+  const bool narrow = total < (1ll << 32);
   const uint32_t check_bytes = static_cast<uint32_t>(k * Q * sizeof(W));
   uint32_t bytes = 0;
   long long item = st * T;
   const long long end = (st * T + T < total) ? st * T + T : total;
   while (item < end) {
-    const long long slot = item / M;
+    const long long slot = div_m(item, M, narrow);
     const int c0 = static_cast<int>(item - slot * M);
     long long run = M - c0;
     if (item + run > end) run = end - item;
@@ -93,6 +100,7 @@ __global__ void __launch_bounds__(256)
   const size_t tile_floats = (size_t)CPW * k * Q;
   W *stages = reinterpret_cast<W *>(smem_raw + 128 * 8) + (size_t)wib * S * tile_floats;
   const long long total = (long long)n_frames_of(fs) * M;
+  const bool narrow = total < (1ll << 32);
   const long long n_tiles = (total + CPW - 1) / CPW;
   const long long gw = (long long)blockIdx.x * nwarps + wib;
   const long long nw = (long long)gridDim.x * nwarps;
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(256)
     }
     const long long item = tile * CPW + ci;
     if (item < total) {
-      const int c = static_cast<int>(item % M);
+      const int c = static_cast<int>(item - div_m(item, M, narrow) * M);
       W *s = stages + (size_t)b * tile_floats + (size_t)ci * k * Q;
       // index maps of the k edges at this lane's EPL entries
       uint32_t pw[KMAX][(EPL + 3) / 4];
