@@ -47,7 +47,7 @@ FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 MEASURED_TRAFFIC = {
     ("var", "fwht", "gf256_n512_k4"): {
         "bytes_per_frame": (272718592 + 219511040) / 256,
-        "sources": ["kernels_var_fwht8.cu", "device_common.cuh", "bulk_copy.cuh"],
+        "sources": ["kernels_var_fwht8x2.cu", "device_common.cuh", "bulk_copy.cuh"],
         "sha256_16": "b4f14737a75b3fdd"},
     ("check", "fwht", "gf256_n512_k4"): {
         "bytes_per_frame": (268608512 + 214977792) / 256,

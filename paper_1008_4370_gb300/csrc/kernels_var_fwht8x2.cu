@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
 
 namespace {
 // launch shape: warps per block, pipeline depth, blocks per SM
-constexpr int kX2Warps = 4, kX2Stages = 3, kX2MinBlocks = 3;
+constexpr int kX2Warps = 4, kX2Stages = 2, kX2MinBlocks = 4;
 template <typename W>
 constexpr size_t x2_smem() {
   return sizeof(X2Stage<W, kX2Stages>) * kX2Warps;
