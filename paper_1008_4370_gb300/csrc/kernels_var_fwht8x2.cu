@@ -86,6 +86,45 @@ __device__ __forceinline__ void transpose(float2 (&v)[16], float2 *s, int o0, in
   __syncwarp();
 }
 
+// One vector (M) as 8 pairs u[i] = (entry i, entry i + 8): register bits 0..2 pair up across
+// the float2 values, register bit 3 lies inside each float2.
+template <int R>
+__device__ __forceinline__ void stage_one(float2 (&u)[8]) {
+  if constexpr (R < 3) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (!(i & (1 << R))) bfly(u[i], u[i | (1 << R)]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float a = u[i].x, b = u[i].y;
+      u[i] = make_float2(a + b, a - b);
+    }
+  }
+}
+__device__ __forceinline__ void stages4_one(float2 (&u)[8]) {
+  stage_one<0>(u);
+  stage_one<1>(u);
+  stage_one<2>(u);
+  stage_one<3>(u);
+}
+// P1 -> P0 for one vector per half-warp in 32-bit words: entry x of half-warp h at float
+// 2 (sum x_i w_i) + h of the warp's whole scratch, so the two half-warps take the even and the
+// odd banks and all 32 lanes hit different banks.
+__device__ __forceinline__ void transpose_one_to0(float2 (&u)[8], float *s, int o0, int o1,
+                                                  int h) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    s[2 * (o1 + roff1(i)) + h] = u[i].x;
+    s[2 * (o1 + roff1(i + 8)) + h] = u[i].y;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    u[i] = make_float2(s[2 * (o0 + roff0(i)) + h], s[2 * (o0 + roff0(i + 8)) + h]);
+  __syncwarp();
+}
+
 __device__ __forceinline__ float4 load4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ float4 load4(const __half *p) {
   const uint2 w = *reinterpret_cast<const uint2 *>(p);
@@ -318,18 +357,18 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         }
       }
     } else {
-      // inverse-direction transform of M (as float2 with an unused half), P1 -> P0, then
-      // stored in natural order for the read-out
+      // inverse-direction transform of M, P1 -> P0, then stored in natural order for the read-out
+      float2 mp[8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) c[j] = make_float2(mu[j], 0.0f);
-      stages4(c);
-      transpose<false>(c, sbuf, o0, o1);
-      stages4(c);
+      for (int i = 0; i < 8; ++i) mp[i] = make_float2(mu[i], mu[i + 8]);
+      stages4_one(mp);
+      transpose_one_to0(mp, reinterpret_cast<float *>(ws.scratch), o0, o1, sub);
+      stages4_one(mp);
       float *m_nat = reinterpret_cast<float *>(sbuf);
-#pragma unroll
-      for (int g = 0; g < 4; ++g)
-        *reinterpret_cast<float4 *>(m_nat + 4 * l + 64 * g) =
-            make_float4(c[4 * g].x, c[4 * g + 1].x, c[4 * g + 2].x, c[4 * g + 3].x);
+      *reinterpret_cast<float4 *>(m_nat + 4 * l) = make_float4(mp[0].x, mp[1].x, mp[2].x, mp[3].x);
+      *reinterpret_cast<float4 *>(m_nat + 4 * l + 64) = make_float4(mp[4].x, mp[5].x, mp[6].x, mp[7].x);
+      *reinterpret_cast<float4 *>(m_nat + 4 * l + 128) = make_float4(mp[0].y, mp[1].y, mp[2].y, mp[3].y);
+      *reinterpret_cast<float4 *>(m_nat + 4 * l + 192) = make_float4(mp[4].y, mp[5].y, mp[6].y, mp[7].y);
       __syncwarp();
       // TENTATIVE: signs of M at alpha^{i-1}, H_e1 alpha^{i-1} (round 0) and H_e2 alpha^{i-1}
       // (round 1), gathered with ballots; bit 16 sub + l belongs to this half-warp
