@@ -294,11 +294,12 @@ __global__ void __launch_bounds__(128)
            int32_t *__restrict__ stats) {
   __shared__ uint8_t gexp[512];
   __shared__ uint8_t glog[256];
+  // the field tables are constant: load them while the previous kernel drains
+  for (int i = threadIdx.x; i < 2 * q; i += blockDim.x) gexp[i] = gexp_g[i];
+  for (int i = threadIdx.x; i < q; i += blockDim.x) glog[i] = glog_g[i];
   griddep_wait();
   griddep_release();
   const int iter = iter_dev ? *iter_dev : iter_arg;
-  for (int i = threadIdx.x; i < 2 * q; i += blockDim.x) gexp[i] = gexp_g[i];
-  for (int i = threadIdx.x; i < q; i += blockDim.x) glog[i] = glog_g[i];
   __syncthreads();
   const int nf = frame_count(fs);
   for (int s = blockIdx.x; s < nf; s += gridDim.x) {
