@@ -43,16 +43,16 @@ FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 # their concatenation at capture time. A changed source voids the figure (reported as null).
 # Capture: ncu --set full --clock-control none -k regex:<kernel> -s 2 -c 1 python bench.py
 #          --frames 256 --steps 1 --warmup 1 --no-cpu-baseline --serve-requests 0 --plain-steps 0
-#          --batches 1 --form fwht
+#          --batches 1 --form fwht --store16-steps 0 --uneven-steps 0
 MEASURED_TRAFFIC = {
     ("var", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (272718592 + 219511040) / 256,
+        "bytes_per_frame": (272737280 + 220424960) / 256,
         "sources": ["kernels_var_fwht8x2.cu", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "b4f14737a75b3fdd"},
+        "sha256_16": "f4d59803ec138a27"},
     ("check", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (268608512 + 214977792) / 256,
+        "bytes_per_frame": (268615168 + 214631424) / 256,
         "sources": ["kernels_check.cu", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "799a4beb2634e8b1"},
+        "sha256_16": "447606c123dee75a"},
 }
 
 
