@@ -312,6 +312,30 @@ def test_decode_full_size_gf256_n512(dev, form):
     assert it_h.min() >= 1 and it_h.max() <= 100 and np.all(it_h[~ok_h] == 100)
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_decode_full_size_gf64_n1200(dev, form):
+    """The plain batched configuration: GF(64) (2,6) N=1200, 4096 frames per launch, Eb/N0 over
+    1.0 .. 3.0 dB (here 2.5 dB, where most frames decode), random codewords. Two sampled frames
+    are decoded by the oracle too (4 iterations); with 100 iterations every frame is checked for
+    what holds at any size."""
+    c = synth.named_code("gf64_n1200_k6")
+    enc = synth.Encoder(c)
+    tx, llr = synth.frames(c, 4096, 2.5, snr_idx=3, encoder=enc)
+    _decode_vs_oracle(dev, c, llr, 4, frames=[7, 4095], min_frac=1.0, form=form)
+    code = nb.Code(c)
+    sym, ok, it = nb.decode(code, _t(llr, dev), 100, form)
+    ex = torch.empty((4096, code.M), dtype=torch.int16, device=dev)
+    nb.nbfd_syndrome(code.handle, 4096, sym, None, None, ex)
+    torch.cuda.synchronize()
+    ok_h = ok.cpu().numpy().astype(bool)
+    assert np.array_equal(ok_h, ~ex.cpu().numpy().any(axis=1))
+    it_h = it.cpu().numpy()
+    assert it_h.min() >= 1 and it_h.max() <= 100 and np.all(it_h[~ok_h] == 100)
+    sym_h = sym.cpu().numpy().astype(np.int64)
+    assert np.mean(np.all(sym_h[ok_h] == tx[ok_h], axis=1)) > 0.999
+    assert ok_h.mean() > 0.9
+
+
 @pytest.mark.parametrize("form", [nb.FORM_BF16_HGEMM, nb.FORM_FP16_HGEMM])
 def test_decode_low_precision_forms_gf256_n512(dev, form):
     """BF16 / FP16 operand forms on the measured configuration. What holds at any precision is
