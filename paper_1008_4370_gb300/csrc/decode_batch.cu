@@ -99,7 +99,8 @@ int tune_code(const nbfd_code *c, int F, int form, const float *llr, float *v2c,
   if (best_ms < 0.0f) return set_error(NBFD_ECUDA, "autotune: no check-kernel shape ran");
   best_ms = -1.0f;
   const std::vector<int> var_bps =
-      (form & 0xff) == NBFD_FORM_FP32_FWHT && c->m == 8 ? std::vector<int>{1, 2, 3, 4}
+      (form & 0xff) == NBFD_FORM_FP32_FWHT && (c->m == 8 || var_fwht6x8_applies(c))
+          ? std::vector<int>{1, 2, 3, 4}
                                                           : std::vector<int>{1, 2, 4, 8, 16};
   for (int bps : var_bps) {
     VarTune vt{bps};

@@ -300,7 +300,10 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
     case 3: NBFD_VAR_FWHT(3) break;
     case 4: NBFD_VAR_FWHT(4) break;
     case 5: NBFD_VAR_FWHT(5) break;
-    case 6: NBFD_VAR_FWHT(6) break;
+    case 6:
+      if (var_fwht6x8_applies(c))
+        return launch_var_fwht6x8(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
+      NBFD_VAR_FWHT(6) break;
     case 7: NBFD_VAR_FWHT(7) break;
     case 8: return launch_var_fwht8x2(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune, false);
     default: return cudaErrorInvalidValue;

@@ -41,7 +41,8 @@ def _code(spec):
 
 # small codes over every field size the kernels are instantiated for, plus the configured codes
 STEP_CODES = [
-    "gf4_n8_k4", (3, 12, 4, 21), "gf16_n32_k4", (5, 20, 4, 22), (6, 24, 6, 23), (7, 16, 4, 24),
+    "gf4_n8_k4", (3, 12, 4, 21), "gf16_n32_k4", (5, 20, 4, 22), (6, 24, 6, 23), (6, 30, 6, 28),
+    (7, 16, 4, 24),
     (8, 16, 4, 25), (4, 80, 20, 26), (8, 64, 16, 27),
 ]
 

@@ -64,7 +64,8 @@ def test_frames_are_seeded():
 
 def test_every_gpu_test_code_can_be_built():
     """The GPU tests build these codes; construct them here so input problems show up on CPU."""
-    specs = [(2, 8, 4, 7), (3, 12, 4, 21), (4, 32, 4, 1), (5, 20, 4, 22), (6, 24, 6, 23), (7, 16, 4, 24),
+    specs = [(2, 8, 4, 7), (3, 12, 4, 21), (4, 32, 4, 1), (5, 20, 4, 22), (6, 24, 6, 23), (6, 30, 6, 28),
+             (7, 16, 4, 24),
              (8, 16, 4, 25), (4, 80, 20, 26), (8, 64, 16, 27)]
     for m, N, k, seed in specs:
         c = synth.regular_code(N, k, m, seed=seed)
