@@ -298,7 +298,7 @@ cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, c
   switch (c->m) {
     case 2: NBFD_VAR_FWHT(2) break;
     case 3: NBFD_VAR_FWHT(3) break;
-    case 4: NBFD_VAR_FWHT(4) break;
+    case 4: return launch_var_fwht4(c, fs, llr, c2v, v2c, sym, fsyn, s, symbol, tune);
     case 5: NBFD_VAR_FWHT(5) break;
     case 6:
       if (var_fwht6x8_applies(c))

@@ -105,6 +105,10 @@ cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
                             cudaStream_t s, bool symbol, VarTune tune = {});
+// GF(16): one lane per variable, every stage in registers
+cudaError_t launch_var_fwht4(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
+                             float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s,
+                             bool symbol, VarTune tune = {});
 // GF(64) with N % 8 == 0: eight variables per warp, 16 entries per lane, one transpose per
 // transform
 bool var_fwht6x8_applies(const nbfd_code *c);
