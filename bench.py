@@ -558,9 +558,6 @@ def run_ours(a):
                    "unit": "Mbit/s", "ms_per_step": ms16, "steps": a.store16_steps,
                    "fer": fails16 / (F * min(len(batches), a.store16_steps)),
                    "message_bytes_per_frame_iteration": 4 * E * q * 2 + N * m * 4}
-    uneven = None
-    if a.uneven_steps > 0 and world == 1 and (form & 0xff) in (FORMS["fwht"], FORMS["direct"]):
-        uneven = uneven_leg(nb, torch, dev, form, a.uneven_steps, a.max_iter)
     served = None
     if a.serve_requests > 0 and world == 1:
         R = a.serve_requests
@@ -575,6 +572,11 @@ def run_ours(a):
         got2, wall2 = serve_run(nb, [(code, llr_req, arr, a.max_iter, info_bits)], form, 32 << 30)
         ld = serve_summary(got2, wall2, a.serve_load)
         served = {"form": a.form, "saturation": sat, "poisson": ld}
+    # the uneven five-code batch last: it holds about 9 GB while it runs
+    uneven = None
+    if a.uneven_steps > 0 and world == 1 and (form & 0xff) in (FORMS["fwht"], FORMS["direct"]):
+        uneven = uneven_leg(nb, torch, dev, form, a.uneven_steps, a.max_iter)
+        torch.cuda.empty_cache()
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
