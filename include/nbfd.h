@@ -187,6 +187,14 @@ int nbfd_autotune(const nbfd_code *code, int n_frames, int form, void *cuda_stre
 int nbfd_autotune_result(const nbfd_code *code, int n_frames, int form, int *check_warps,
                          int *check_stages, int *check_blocks_per_sm, int *var_blocks_per_sm);
 
+/*
+ * nbfd_last_decode_stats -- for the calling thread's last successful nbfd_decode: the number of
+ * (frame, iteration) pairs where the Fourier-domain syndrome of Section 3.2 cleared while the
+ * GF(2^m) syndrome H x_hat was not 0 (the frame went on decoding: the stop test needs both).
+ * Errors: NBFD_EINVAL (NULL pointer, or no such call in this thread).
+ */
+int nbfd_last_decode_stats(long long *fourier_only_clears);
+
 /* ---- decoding without device allocation ----------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers of the library. */
 

@@ -198,6 +198,7 @@ def decode(code: OracleCode, llr: np.ndarray, max_iter: int, trace: bool = False
     fok = False
     margins = []
     hist = []
+    fourier_only = 0  # iterations whose Fourier-domain syndrome cleared while H x_hat != 0
     it = 0
     for it in range(1, max_iter + 1):
         c2v = check_update(code, v2c)
@@ -214,11 +215,14 @@ def decode(code: OracleCode, llr: np.ndarray, max_iter: int, trace: bool = False
             fok = not np.any(fs)
         es = code.syndrome(x_hat)
         ok = not np.any(es)
+        if decision != "symbol" and fok and not ok:
+            fourier_only += 1
         if trace:
             hist.append({"c2v": c2v, "v2c": v2c, "M": M, "x": x_hat.copy()})
         if fok and ok:
             break
-    out = {"symbols": x_hat, "ok": bool(ok), "iters": it, "fourier_ok": bool(fok), "margins": margins}
+    out = {"symbols": x_hat, "ok": bool(ok), "iters": it, "fourier_ok": bool(fok), "margins": margins,
+           "fourier_only": fourier_only}
     if trace:
         out["trace"] = hist
     return out

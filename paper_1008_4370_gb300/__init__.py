@@ -20,6 +20,7 @@ __all__ = [
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
     "STORE_F16", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
+    "nbfd_last_decode_stats",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
     "nbfd_srv_poll", "nbfd_srv_stats", "nbfd_srv_destroy", "nbfd_srv_clock", "nbfd_srv_submit_many",
@@ -57,6 +58,7 @@ SIGNATURES = [
     ("nbfd_autotune", _I, [_P, _I, _I, _P]),
     ("nbfd_init_messages_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_diag_wait_expiry", _I, [ctypes.c_longlong, _P]),
+    ("nbfd_last_decode_stats", _I, [_P]),
     ("nbfd_check_update_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P]),
     ("nbfd_init_messages", _I, [_P, _I, _P, _P, _P, _P]),
@@ -191,6 +193,14 @@ def nbfd_decode(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, ite
 
 BATCH_AUTOTUNE = 1
 STORE_F16 = 0x200  # form flag: messages stored as IEEE half (FWHT form, m = 8)
+
+
+def nbfd_last_decode_stats():
+    """(frame, iteration) pairs of this thread's last nbfd_decode where the Fourier-domain
+    syndrome cleared while H x_hat != 0."""
+    v = ctypes.c_longlong()
+    _check(lib().nbfd_last_decode_stats(ctypes.byref(v)))
+    return v.value
 
 
 def nbfd_diag_wait_expiry(budget_cycles, stream=None):

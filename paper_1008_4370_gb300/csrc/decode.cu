@@ -162,6 +162,9 @@ extern "C" size_t nbfd_decode_workspace_size(const nbfd_code *c, int n_frames, i
   return carve(c, n_frames, max_iter, form, nullptr).bytes;
 }
 
+// the disagreement count of the calling thread's last nbfd_decode (nbfd_last_decode_stats)
+thread_local long long g_last_fourier_only = -1;
+
 // A pinned host word per host thread for the active-frame count, allocated on first use and kept
 // for the thread's lifetime (a per-call cudaMallocHost / cudaFreeHost pair would synchronise the
 // device).
@@ -179,6 +182,13 @@ static int32_t *pinned_word() {
     h.p = static_cast<int32_t *>(p);
   }
   return h.p;
+}
+
+extern "C" int nbfd_last_decode_stats(long long *fourier_only_clears) {
+  if (!fourier_only_clears) return set_error(NBFD_EINVAL, "NULL pointer");
+  if (g_last_fourier_only < 0) return set_error(NBFD_EINVAL, "no nbfd_decode in this thread yet");
+  *fourier_only_clears = g_last_fourier_only;
+  return NBFD_OK;
 }
 
 extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
@@ -206,6 +216,7 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
   const bool f16 = stores_f16(form);
   int32_t *host_count = nullptr;
   int st = NBFD_OK;
+  g_last_fourier_only = -1;
   int prof_mask;
   {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -274,14 +285,17 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       active = *host_count;
     }
     if (st == NBFD_OK) {
-      // stats[1] holds NBFD_ETIMEDOUT if a bounded device-side wait expired
-      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.stats + 1, sizeof(int32_t),
+      // stats[0] counts iterations where a frame's Fourier-domain syndrome cleared while its
+      // GF(2^m) syndrome did not; stats[1] holds NBFD_ETIMEDOUT if a bounded wait expired
+      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.stats, 2 * sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s),
                            "cudaMemcpyAsync(status)")))
         break;
       if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
-      if (*host_count != 0)
-        st = set_error(NBFD_ETIMEDOUT, "a bounded device-side wait expired (status %d)", *host_count);
+      g_last_fourier_only = host_count[0];
+      if (host_count[1] != 0)
+        st = set_error(NBFD_ETIMEDOUT, "a bounded device-side wait expired (status %d)",
+                       host_count[1]);
     }
     if (st == NBFD_OK && tm.on()) {
       std::vector<int32_t> counts((size_t)max_iter + 2, 0);

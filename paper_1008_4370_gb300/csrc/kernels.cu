@@ -304,19 +304,29 @@ __global__ void __launch_bounds__(128)
   const int nf = frame_count(fs);
   for (int s = blockIdx.x; s < nf; s += gridDim.x) {
     const int f = frame_at(fs, s);
-    int ffail = 0, efail = 0;
+    // Fourier-domain syndrome first (one byte per edge); the GF(2^m) syndrome, which gathers
+    // the decisions, only where the outcome depends on it: when the Fourier-domain syndrome
+    // clears, and at max_iter (the flag of a frame that never stopped)
+    int ffail = 0;
     for (int c = threadIdx.x; c < M; c += blockDim.x) {
-      int fsv = 0, esv = 0;
-      for (int j = 0; j < k; ++j) {
-        const int e = c * k + j;
-        fsv ^= fsyn[(size_t)f * E + e];
-        esv ^= gf_mul(__ldg(edge_h + e), sym[(size_t)f * N + __ldg(edge_var + e)], gexp, glog);
-      }
+      int fsv = 0;
+      for (int j = 0; j < k; ++j) fsv ^= fsyn[(size_t)f * E + c * k + j];
       ffail |= fsv != 0;
-      efail |= esv != 0;
     }
     ffail = __syncthreads_or(ffail);
-    efail = __syncthreads_or(efail);
+    int efail = 1;
+    if (!ffail || iter >= max_iter) {
+      efail = 0;
+      for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        int esv = 0;
+        for (int j = 0; j < k; ++j) {
+          const int e = c * k + j;
+          esv ^= gf_mul(__ldg(edge_h + e), sym[(size_t)f * N + __ldg(edge_var + e)], gexp, glog);
+        }
+        efail |= esv != 0;
+      }
+      efail = __syncthreads_or(efail);
+    }
     if (threadIdx.x == 0) {
       if (!ffail && !efail) {
         ok[f] = 1;
@@ -327,7 +337,8 @@ __global__ void __launch_bounds__(128)
       } else {
         next_list[atomicAdd(next_count, 1)] = f;
       }
-      if (ffail != efail) atomicAdd(stats, 1);
+      // frames whose Fourier-domain syndrome cleared while H x_hat != 0 (the two differ)
+      if (!ffail && efail) atomicAdd(stats, 1);
     }
   }
 }

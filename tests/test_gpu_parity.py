@@ -250,6 +250,31 @@ def test_decode_parity_tiny_gf16(dev, form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_fourier_only_clears_count(dev, form):
+    """nbfd_last_decode_stats counts the (frame, iteration) pairs where the Fourier-domain
+    syndrome cleared while H x_hat != 0 (reading of Section 3.2: the stop test needs both); one
+    frame per call, compared with the oracle's count on frames whose margins are clear."""
+    c = synth.named_code("gf4_n8_k4")
+    oc = OracleCode.from_dict(c)
+    code = nb.Code(c)
+    _, llr = synth.frames(c, 100, -1.0, batch_idx=5)  # low SNR: the case occurs
+    n_cmp = n_hit = total = 0
+    for f in range(100):
+        nb.decode(code, _t(llr[f:f + 1], dev), 20, form)
+        torch.cuda.synchronize()
+        got = nb.nbfd_last_decode_stats()
+        assert got >= 0
+        total += got
+        r = LF.decode(oc, llr[f].astype(np.float64), 20)
+        if min(r["margins"]) > MARGIN:
+            n_cmp += 1
+            n_hit += r["fourier_only"] > 0
+            assert got == r["fourier_only"], (f, got, r["fourier_only"])
+    assert n_cmp > 30 and n_hit >= 2, (n_cmp, n_hit)
+    print(f"fourier-only clears: {total} over 100 frames")
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_decode_parity_gf4_n8(dev, form):
     c = synth.named_code("gf4_n8_k4")
     _, llr = synth.frames(c, 64, 1.0)
