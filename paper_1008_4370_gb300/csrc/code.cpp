@@ -2,6 +2,10 @@
 // tables and the Fourier index maps (Appendix A), and the device copies the kernels read.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <map>
+#include <mutex>
+
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -33,11 +37,41 @@ int check_cuda(cudaError_t e, const char *what) {
   return set_error(NBFD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// SM count of the current device, looked up once per device (launch sizing runs per launch)
 int sm_count() {
+  static std::atomic<int> cache[64];
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev >= 0 && dev < 64) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-  return n > 0 ? n : 1;
+  n = n > 0 ? n : 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+// Raises the dynamic shared-memory limit of `kernel` on the current device to `bytes` once, not
+// at every launch.
+cudaError_t ensure_smem(const void *kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find({kernel, dev});
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  }
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &v = done[{kernel, dev}];
+    v = v > bytes ? v : bytes;
+  }
+  return e;
 }
 
 // GF(2^m) by the linear-feedback recurrence alpha^{i+1} = alpha * alpha^i mod poly.

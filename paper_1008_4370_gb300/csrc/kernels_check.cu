@@ -242,8 +242,8 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
   if (grid < 1) grid = 1;
 #define NBFD_CHK_T(MB, KM, W)                                                                \
   {                                                                                           \
-    cudaFuncSetAttribute(k_check_warp<MB, KM, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,\
-                         (int)smem);                                                          \
+    const cudaError_t ae = ensure_smem((const void *)k_check_warp<MB, KM, W>, smem);          \
+    if (ae != cudaSuccess) return ae;                                                         \
     const cudaError_t le = launch_dependent(                                                  \
         k_check_warp<MB, KM, W>, dim3((int)grid), dim3(warps * 32), smem, s,                  \
         reinterpret_cast<const W *>(v2c), reinterpret_cast<W *>(c2v), c->d_edge_h, c->d_perm, \

@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   for (; t < n_units; ++t) {
     const int b = static_cast<int>(t % S);
     if (t + S - 1 < n_units) {
-      if (lane == 0) fence_proxy_async_smem();
+      // every issuing lane orders the warp's earlier generic accesses of the stage it refills
+      // (made visible to it by the loop-end __syncwarp) before its bulk copies
+      fence_proxy_async_smem();
       __syncwarp();
       issue(static_cast<int>((t + S - 1) % S), __shfl_sync(kFull, pf_f, 0),
             __shfl_sync(kFull, pf_v, 0));
@@ -375,8 +377,7 @@ cudaError_t launch_var_fwht6x8(const nbfd_code *c, FrameSet fs, const float *llr
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   auto go = [&](auto kern) -> cudaError_t {
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(x8_smem()));
+    const cudaError_t e = ensure_smem((const void *)kern, x8_smem());
     if (e != cudaSuccess) return e;
     return launch_dependent(kern, dim3((int)grid), dim3(32 * kX8Warps), x8_smem(), s, llr, c2v,
                             v2c, sym, fsyn, c->d_var_edges, c->d_edge_z, c->N, c->E, fs, err);

@@ -421,8 +421,7 @@ cudaError_t launch_var_fwht8x2(const nbfd_code *c, FrameSet fs, const float *llr
   if (g < 1) g = 1;
   auto go = [&](auto kern, auto tag) -> cudaError_t {
     using W = decltype(tag);
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(x2_smem<W>()));
+    const cudaError_t e = ensure_smem((const void *)kern, x2_smem<W>());
     if (e != cudaSuccess) return e;
     return launch_dependent(kern, dim3((int)g), dim3(32 * kX2Warps), x2_smem<W>(), s, llr,
                             reinterpret_cast<const W *>(c2v), reinterpret_cast<W *>(v2c), sym,

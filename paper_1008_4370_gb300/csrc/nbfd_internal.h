@@ -59,6 +59,7 @@ bool tune_lookup(const nbfd_code *c, int F, int form, CheckTune *ct, VarTune *vt
 int set_error(int status, const char *fmt, ...);
 int check_cuda(cudaError_t e, const char *what);
 int sm_count();
+cudaError_t ensure_smem(const void *kernel, size_t bytes);
 
 // Launch with programmatic stream serialization: the kernel may be scheduled while the previous
 // kernel of the stream still runs, and must call griddep_wait() before reading its outputs.
