@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256)
       for (long long j = i; j < issued; ++j)
         mbar_wait_bounded(&bars[j % S], static_cast<uint32_t>((j / S) & 1));
     }
-    bulk_wait_all();
+    bulk_wait_read_all();  // the CTA's shared memory must outlive the bulk stores' reads
   }
 }
 
