@@ -311,10 +311,14 @@ def uneven_leg(nb, torch, dev, form, steps, max_iter):
 
 def serve_run(nb, streams, form, budget, poll_sleep=2e-4, timeout=300.0):
     """Drive the serving loop. streams: list of (code, llr [R][N][m], arrivals (s, relative, sorted)
-    or None for 'all at t = 0', max_iter, info_bits). Returns per-request (ok, iters, latency, bits)
-    plus the wall time from the first arrival to the last retirement."""
+    or None for 'all at t = 0', max_iter, info_bits). Returns per-request (ok, iters, latency, bits),
+    the wall time from the first arrival to the last retirement and the worker's time per phase.
+    The codes' pools are created before the clock starts (a server registers its codes at
+    start-up)."""
     srv = nb.nbfd_srv_create(budget, form)
     try:
+        for code, _, _, _, _ in streams:
+            nb.nbfd_srv_register(srv, code.handle)
         t0 = nb.nbfd_srv_clock()
         events = []  # (arrival, stream index, frame index)
         for si, (_, llr, arr, _, _) in enumerate(streams):
@@ -338,7 +342,9 @@ def serve_run(nb, streams, form, budget, poll_sleep=2e-4, timeout=300.0):
                 for si, lst in by.items():
                     code, llr, _, max_iter, bits = streams[si]
                     idx = np.array([i for _, i in lst])
-                    tk = nb.nbfd_srv_submit_many(srv, code.handle, llr[idx], max_iter,
+                    run = len(idx) > 0 and idx[-1] - idx[0] + 1 == len(idx) and bool(np.all(np.diff(idx) == 1))
+                    x = llr[idx[0]:idx[-1] + 1] if run else llr[idx]  # a view when the frames are consecutive
+                    tk = nb.nbfd_srv_submit_many(srv, code.handle, x, max_iter,
                                                  np.array([t0 + t for t, _ in lst]))
                     for t in tk.tolist():
                         bits_of[t] = bits
@@ -351,18 +357,19 @@ def serve_run(nb, streams, form, budget, poll_sleep=2e-4, timeout=300.0):
             if len(tk) == 0:
                 time.sleep(poll_sleep)
         wall = nb.nbfd_srv_clock() - t0
+        phases = nb.nbfd_srv_worker_times(srv)
     finally:
         nb.nbfd_srv_destroy(srv)
-    return got, wall
+    return got, wall, phases
 
 
-def serve_summary(got, wall, offered=None):
+def serve_summary(got, wall, phases, offered=None):
     lat = np.array([g[2] for g in got])
     bits = sum(g[3] for g in got)
     return {"requests": len(got), "mbit_s": bits / wall / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "fer": float(np.mean([1 - g[0] for g in got])),
             "mean_iterations": float(np.mean([g[1] for g in got])), "offered_frames_s": offered,
-            "wall_s": wall}
+            "wall_s": wall, "worker_s": {k: round(v, 4) for k, v in phases.items()}}
 
 
 def run_serve_sweep(a):
@@ -397,9 +404,9 @@ def run_serve_sweep(a):
             ebn0 = rng.uniform(1.5, 3.5, size=len(sel))
             _, llr = synth.frames(c, len(sel), ebn0, snr_idx=ci, batch_idx=int(lam) % 100000, encoder=enc)
             streams.append((code, llr, arr[sel], 100, bits))
-        got, wall = serve_run(nb, streams, FORMS[a.form] if FORMS[a.form] in (0, 3) else FORMS["fwht"],
-                              40 << 30)
-        print(json.dumps({"serving_sweep": serve_summary(got, wall, lam), "form": a.form}), flush=True)
+        got, wall, ph = serve_run(nb, streams, FORMS[a.form] if FORMS[a.form] in (0, 3) else FORMS["fwht"],
+                                  40 << 30)
+        print(json.dumps({"serving_sweep": serve_summary(got, wall, ph, lam), "form": a.form}), flush=True)
 
 
 def run_ours(a):
@@ -565,12 +572,12 @@ def run_ours(a):
         llr_all = np.concatenate(pool, axis=0)
         reps = (R + llr_all.shape[0] - 1) // llr_all.shape[0]
         llr_req = np.concatenate([llr_all] * reps, axis=0)[:R]
-        got, wall = serve_run(nb, [(code, llr_req, None, a.max_iter, info_bits)], form, 32 << 30)
-        sat = serve_summary(got, wall)
+        got, wall, ph = serve_run(nb, [(code, llr_req, None, a.max_iter, info_bits)], form, 32 << 30)
+        sat = serve_summary(got, wall, ph)
         rng = synth.rng_for(23, R)
         arr = np.cumsum(rng.exponential(1.0 / a.serve_load, size=R))
-        got2, wall2 = serve_run(nb, [(code, llr_req, arr, a.max_iter, info_bits)], form, 32 << 30)
-        ld = serve_summary(got2, wall2, a.serve_load)
+        got2, wall2, ph2 = serve_run(nb, [(code, llr_req, arr, a.max_iter, info_bits)], form, 32 << 30)
+        ld = serve_summary(got2, wall2, ph2, a.serve_load)
         served = {"form": a.form, "saturation": sat, "poisson": ld}
     # the uneven five-code batch last: it holds about 9 GB while it runs
     uneven = None

@@ -291,9 +291,14 @@ int nbfd_syndrome(const nbfd_code *code, int n_frames, const uint16_t *symbols_d
 typedef struct nbfd_server nbfd_server;
 
 /* Start a server on the current device. mem_budget_bytes bounds the device memory of all pools
- * (a pool is sized from what is left when its code is first submitted, at most 4096 slots);
- * form is an NBFD_FORM_* for every request. */
+ * (a pool is sized from what is left when its code is first registered or submitted, at most
+ * 4096 slots); form is an NBFD_FORM_* for every request. */
 int nbfd_srv_create(size_t mem_budget_bytes, int form, nbfd_server **out);
+
+/* Create the pool of a code now rather than at its first submission: its device memory, streams
+ * and pinned staging buffers are allocated here, so that the first requests do not wait for
+ * them. Registering a code twice is a no-op. Errors as nbfd_srv_submit. */
+int nbfd_srv_register(nbfd_server *srv, const nbfd_code *code);
 
 /* Queue one frame: llr_host [N][m] float32 (copied), max_iter >= 1. *ticket identifies it.
  * NBFD_EBUSY: no pool fits the remaining budget or the queue is full -- retry later.
@@ -312,7 +317,9 @@ double nbfd_srv_clock(void);
 
 /* Queue n frames of one code at once: llr_host [n][N][m]; arrival (may be NULL) gives each
  * frame's arrival time on nbfd_srv_clock() -- latency is then measured from it; tickets [n] out.
- * Errors as nbfd_srv_submit (no frame is queued on error). */
+ * All n tickets and the queue room are taken before any frame is copied; the frames are then
+ * copied and queued in chunks, so the worker may start on the first frames before the call
+ * returns. Errors as nbfd_srv_submit (no frame is queued on error). */
 int nbfd_srv_submit_many(nbfd_server *srv, const nbfd_code *code, int n, const float *llr_host,
                          int max_iter, const double *arrival, uint64_t *tickets);
 
@@ -326,7 +333,14 @@ int nbfd_srv_collect(nbfd_server *srv, int max_n, uint64_t *tickets, uint8_t *ok
 int nbfd_srv_stats(nbfd_server *srv, long long *rounds, long long *queued, long long *in_flight,
                    size_t *device_bytes);
 
-/* Stop the worker and free the pools (pending requests are dropped). */
+/* Cumulative wall seconds the worker thread has spent in each phase since the server started:
+ * seconds[0] admission (moving queued frames into free slots and staging their LLRs in pinned
+ * memory), [1] issuing rounds (launches and copies), [2] waiting for the oldest round on the
+ * device, [3] retiring (result copies, ticket completion), [4] idle (no work). seconds [5] out. */
+int nbfd_srv_worker_times(nbfd_server *srv, double *seconds);
+
+/* Stop the worker and free the pools (pending requests are dropped). No other call on srv may
+ * run concurrently with this one. */
 void nbfd_srv_destroy(nbfd_server *srv);
 
 /* ---- kernel timers (CUDA events around every launch of nbfd_decode) -------------------- */

@@ -24,7 +24,7 @@ __all__ = [
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
     "nbfd_srv_poll", "nbfd_srv_stats", "nbfd_srv_destroy", "nbfd_srv_clock", "nbfd_srv_submit_many",
-    "nbfd_srv_collect",
+    "nbfd_srv_collect", "nbfd_srv_register", "nbfd_srv_worker_times",
 ]
 
 FORM_FP32_DIRECT = 0
@@ -73,6 +73,8 @@ SIGNATURES = [
     ("nbfd_srv_submit_many", _I, [_P, _P, _I, _P, _I, _P, _P]),
     ("nbfd_srv_collect", _I, [_P, _I, _P, _P, _P, _P]),
     ("nbfd_srv_destroy", None, [_P]),
+    ("nbfd_srv_register", _I, [_P, _P]),
+    ("nbfd_srv_worker_times", _I, [_P, _P]),
     ("nbfd_prof_enable", _I, [_I]),
     ("nbfd_prof_get", _I, [_I, _P, _P, _P]),
     ("nbfd_last_error", ctypes.c_char_p, []),
@@ -340,6 +342,18 @@ def nbfd_srv_stats(srv):
     vals = [ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()]
     _check(lib().nbfd_srv_stats(srv, *[ctypes.byref(v) for v in vals]))
     return tuple(v.value for v in vals)
+
+
+def nbfd_srv_register(srv, code_handle):
+    """Create the code's pool now (device memory, streams, pinned staging)."""
+    _check(lib().nbfd_srv_register(srv, code_handle))
+
+
+def nbfd_srv_worker_times(srv):
+    """Cumulative worker seconds per phase: admission, issue, wait, retire, idle."""
+    out = np.zeros(5, dtype=np.float64)
+    _check(lib().nbfd_srv_worker_times(srv, out.ctypes.data))
+    return dict(zip(("admission", "issue", "wait", "retire", "idle"), out.tolist()))
 
 
 def nbfd_srv_destroy(srv):

@@ -11,11 +11,16 @@
 //      Fourier-domain and GF(2^m) syndromes are zero, or that reached its own max_iter, leaves
 //      the active list for a done list;
 //   4. copies the done slots' decisions back, completes their tickets and frees the slots.
+// Rounds are pipelined two deep: the host issues round r, then retires round r-1 and admits
+// and stages round r+1 while round r runs, so its work stays off the device's critical path.
+// The active list is extended on the device, and slots freed by round r-1 are reused from
+// round r+1 on.
 // A frame's arithmetic never involves another frame, so its result is identical alone and in
 // any mix of requests.
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <atomic>
 #include <condition_variable>
 #include <cstdint>
 #include <cstring>
@@ -37,6 +42,8 @@ namespace {
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+enum Phase { kAdmit = 0, kIssue = 1, kWait = 2, kRetire = 3, kIdle = 4 };
 
 // INITIALIZATION for the slots list[0..*count): V->C on both edges of every variable = Lambda0.
 template <int MB>
@@ -139,6 +146,17 @@ __global__ void k_admit(const float *__restrict__ staged, const int32_t *__restr
   }
 }
 
+// Appends the n admitted slots to the active list at its current length on the device (the
+// host does not wait for the previous round's stop test to learn it).
+__global__ void __launch_bounds__(256)
+    k_append(const int32_t *__restrict__ slots, int n, int32_t *__restrict__ list,
+             int32_t *__restrict__ count) {
+  const int base = *count;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) list[base + i] = slots[i];
+  __syncthreads();
+  if (threadIdx.x == 0) *count = base + n;
+}
+
 // Retirement: pack the decisions, flags and iteration counts of the done slots contiguously.
 __global__ void k_gather_done(const int32_t *__restrict__ done_list,
                               const int32_t *__restrict__ done_count,
@@ -171,6 +189,15 @@ struct Result {
   double latency = 0.0;
 };
 
+// Words of Pool::cnt.
+constexpr int kCntActive = 0;  // [0], [1]: lengths of active lists 0 and 1
+constexpr int kCntDone = 2;    // [2], [3]: done-list lengths of the rounds of parity 0 and 1
+constexpr int kCntErr = 4;     // set to NBFD_ETIMEDOUT by a kernel whose bounded wait expired
+constexpr int kCntNew = 5;     // frames admitted by the current round
+
+// Rounds alternate between two parities. Everything a round reads from or writes to the host
+// (staged admissions, counts, packed results) exists once per parity, so the host can stage
+// round r+1 and retire round r-1 while round r runs on the device.
 struct Pool {
   const nbfd_code *code = nullptr;
   int S = 0;  // slots
@@ -180,27 +207,33 @@ struct Pool {
   uint16_t *sym = nullptr;
   uint8_t *fsyn = nullptr, *ok = nullptr;
   int32_t *iter = nullptr, *maxit = nullptr, *lists[2] = {nullptr, nullptr};
-  float *stage_llr = nullptr;                    // [S][N][m] admitted frames, packed
+  float *stage_llr = nullptr;                             // [S][N][m] admitted frames, packed
   int32_t *stage_slot = nullptr, *stage_maxit = nullptr;  // [S]
-  uint16_t *pack_sym = nullptr;                  // [S][N] retired frames, packed
-  uint8_t *pack_ok = nullptr;                    // [S]
-  int32_t *pack_iter = nullptr;                  // [S]
-  int32_t *done_list = nullptr, *cnt = nullptr;  // cnt: [0] active(list 0), [1] active(list 1),
-                                                 // [2] done, [3] new-slot count, [4] error word
-  int cur = 0;
-  int active = 0;  // frames in lists[cur] (known on the host after each round)
+  int32_t *done_list[2] = {nullptr, nullptr};             // [S] per parity
+  uint16_t *pack_sym[2] = {nullptr, nullptr};             // [S][N] retired frames, packed
+  uint8_t *pack_ok[2] = {nullptr, nullptr};               // [S]
+  int32_t *pack_iter[2] = {nullptr, nullptr};             // [S]
+  int32_t *cnt = nullptr;                                 // kCnt* words
+  int cur = 0;  // active list the next round reads
+  int par = 0;  // parity of the next round
+  std::deque<int> issued;  // parities of rounds issued and not yet retired, oldest first
   std::vector<int> free_slots;
-  std::unordered_map<int, Request> in_flight;
+  std::unordered_map<int, Request> in_flight;  // changed only under the server lock
   std::deque<Request> queue;
-  cudaStream_t stream = nullptr;
+  size_t reserved = 0;  // frames a running nbfd_srv_submit_many has counted but not queued yet
+  cudaStream_t stream = nullptr;       // rounds
+  cudaStream_t copy_stream = nullptr;  // result copies, overlapping the next round
+  cudaEvent_t round_done[2] = {nullptr, nullptr};
   // pinned host buffers
-  float *h_llr = nullptr;      // [S][N][m]
-  uint16_t *h_sym = nullptr;   // [S][N]
-  int32_t *h_io = nullptr;     // [S] slot ids in / done list out
-  int32_t *h_small = nullptr;  // [8]: counts, per-slot max_iter staging
-  int32_t *h_maxit = nullptr;  // [S]
-  int32_t *h_iters = nullptr;  // [S]
-  uint8_t *h_ok = nullptr;     // [S]
+  float *h_llr[2] = {nullptr, nullptr};       // [S][N][m] staged admissions
+  int32_t *h_slot[2] = {nullptr, nullptr};    // [S] their slots
+  int32_t *h_maxit[2] = {nullptr, nullptr};   // [S] their max_iter
+  int32_t *h_cnt[2] = {nullptr, nullptr};     // [4]: in: [0] admitted; out: [1] next active,
+                                              // [2] done, [3] error word
+  int32_t *h_done = nullptr;                  // [S] done slots of the round being retired
+  uint16_t *h_sym = nullptr;                  // [S][N]
+  uint8_t *h_ok = nullptr;                    // [S]
+  int32_t *h_iters = nullptr;                 // [S]
 };
 
 }  // namespace
@@ -222,14 +255,37 @@ struct nbfd_server {
   int error = NBFD_OK;
   std::thread worker;
   long long rounds = 0;
+  // worker time per phase, nanoseconds: admission, issue, wait, retire, idle
+  std::atomic<long long> phase_ns[5] = {};
 };
 
 namespace nbfd {
 namespace {
 
 size_t slot_bytes(const nbfd_code *c) {
-  return (size_t)2 * c->E * c->q * 4 + (size_t)2 * c->N * c->m * 4 + (size_t)2 * c->N * 2 + c->E +
-         2 + 8 * 4 + 64;
+  return (size_t)2 * c->E * c->q * 4 + (size_t)2 * c->N * c->m * 4 + (size_t)3 * c->N * 2 + c->E +
+         3 + 10 * 4 + 64;
+}
+
+void free_pool(Pool *p) {
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
+  if (p->block) cudaFree(p->block);
+  if (p->stream) cudaStreamDestroy(p->stream);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (p->round_done[b]) cudaEventDestroy(p->round_done[b]);
+    cudaFreeHost(p->h_llr[b]);
+    cudaFreeHost(p->h_slot[b]);
+    cudaFreeHost(p->h_maxit[b]);
+    cudaFreeHost(p->h_cnt[b]);
+  }
+  cudaFreeHost(p->h_done);
+  cudaFreeHost(p->h_sym);
+  cudaFreeHost(p->h_ok);
+  cudaFreeHost(p->h_iters);
+  p->block = nullptr;
+  p->stream = p->copy_stream = nullptr;
 }
 
 int make_pool(nbfd_server *srv, const nbfd_code *c, Pool **out) {
@@ -251,74 +307,78 @@ int make_pool(nbfd_server *srv, const nbfd_code *c, Pool **out) {
   p->S = static_cast<int>(S);
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t msg = al((size_t)S * c->E * c->q * 4);
-  size_t off[19], o = 0;
-  off[0] = o; o += msg;                                   // v2c
-  off[1] = o; o += msg;                                   // c2v
-  off[2] = o; o += al((size_t)S * c->N * c->m * 4);       // llr
-  off[3] = o; o += al((size_t)S * c->N * 2);              // sym
-  off[4] = o; o += al((size_t)S * c->E);                  // fsyn
-  off[5] = o; o += al((size_t)S);                         // ok
-  off[6] = o; o += al((size_t)S * 4);                     // iter
-  off[7] = o; o += al((size_t)S * 4);                     // maxit
-  off[8] = o; o += al((size_t)S * 4);                     // list 0
-  off[9] = o; o += al((size_t)S * 4);                     // list 1
-  off[10] = o; o += al((size_t)S * 4);                    // done list
-  off[11] = o; o += al(8 * 4);                            // counters
-  off[12] = o; o += al((size_t)S * c->N * c->m * 4);      // staged LLRs
-  off[13] = o; o += al((size_t)S * 4);                    // staged slots
-  off[14] = o; o += al((size_t)S * 4);                    // staged max_iter
-  off[15] = o; o += al((size_t)S * c->N * 2);             // packed decisions
-  off[16] = o; o += al((size_t)S);                        // packed flags
-  off[17] = o; o += al((size_t)S * 4);                    // packed iterations
+  const size_t frames_f = al((size_t)S * c->N * c->m * 4), frames_u16 = al((size_t)S * c->N * 2);
+  const size_t ints = al((size_t)S * 4), bytes = al((size_t)S);
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    const size_t at = o;
+    o += n;
+    return at;
+  };
+  const size_t o_v2c = take(msg), o_c2v = take(msg), o_llr = take(frames_f);
+  const size_t o_sym = take(frames_u16), o_fsyn = take(al((size_t)S * c->E)), o_ok = take(bytes);
+  const size_t o_iter = take(ints), o_maxit = take(ints), o_list0 = take(ints),
+               o_list1 = take(ints), o_cnt = take(al(8 * 4));
+  const size_t o_stage = take(frames_f), o_stage_slot = take(ints), o_stage_maxit = take(ints);
+  size_t o_done[2], o_psym[2], o_pok[2], o_piter[2];
+  for (int b = 0; b < 2; ++b) {
+    o_done[b] = take(ints);
+    o_psym[b] = take(frames_u16);
+    o_pok[b] = take(bytes);
+    o_piter[b] = take(ints);
+  }
   p->bytes = o;
   if (int st = check_cuda(cudaMalloc(&p->block, o), "cudaMalloc(server pool)")) return st;
-  char *b = static_cast<char *>(p->block);
-  p->v2c = reinterpret_cast<float *>(b + off[0]);
-  p->c2v = reinterpret_cast<float *>(b + off[1]);
-  p->llr = reinterpret_cast<float *>(b + off[2]);
-  p->sym = reinterpret_cast<uint16_t *>(b + off[3]);
-  p->fsyn = reinterpret_cast<uint8_t *>(b + off[4]);
-  p->ok = reinterpret_cast<uint8_t *>(b + off[5]);
-  p->iter = reinterpret_cast<int32_t *>(b + off[6]);
-  p->maxit = reinterpret_cast<int32_t *>(b + off[7]);
-  p->lists[0] = reinterpret_cast<int32_t *>(b + off[8]);
-  p->lists[1] = reinterpret_cast<int32_t *>(b + off[9]);
-  p->done_list = reinterpret_cast<int32_t *>(b + off[10]);
-  p->cnt = reinterpret_cast<int32_t *>(b + off[11]);
-  p->stage_llr = reinterpret_cast<float *>(b + off[12]);
-  p->stage_slot = reinterpret_cast<int32_t *>(b + off[13]);
-  p->stage_maxit = reinterpret_cast<int32_t *>(b + off[14]);
-  p->pack_sym = reinterpret_cast<uint16_t *>(b + off[15]);
-  p->pack_ok = reinterpret_cast<uint8_t *>(b + off[16]);
-  p->pack_iter = reinterpret_cast<int32_t *>(b + off[17]);
-  int st = check_cuda(cudaMemset(p->cnt, 0, 32), "cudaMemset");
-  if (!st) st = check_cuda(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking), "stream");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_llr, (size_t)S * c->N * c->m * 4), "pinned");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_sym, (size_t)S * c->N * 2), "pinned");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_io, (size_t)S * 4), "pinned");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_small, 64), "pinned");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_maxit, (size_t)S * 4), "pinned");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_iters, (size_t)S * 4), "pinned");
-  if (!st) st = check_cuda(cudaMallocHost(&p->h_ok, (size_t)S), "pinned");
-  if (st) return st;
-  for (int s = p->S - 1; s >= 0; --s) p->free_slots.push_back(s);
+  char *base = static_cast<char *>(p->block);
+  p->v2c = reinterpret_cast<float *>(base + o_v2c);
+  p->c2v = reinterpret_cast<float *>(base + o_c2v);
+  p->llr = reinterpret_cast<float *>(base + o_llr);
+  p->sym = reinterpret_cast<uint16_t *>(base + o_sym);
+  p->fsyn = reinterpret_cast<uint8_t *>(base + o_fsyn);
+  p->ok = reinterpret_cast<uint8_t *>(base + o_ok);
+  p->iter = reinterpret_cast<int32_t *>(base + o_iter);
+  p->maxit = reinterpret_cast<int32_t *>(base + o_maxit);
+  p->lists[0] = reinterpret_cast<int32_t *>(base + o_list0);
+  p->lists[1] = reinterpret_cast<int32_t *>(base + o_list1);
+  p->cnt = reinterpret_cast<int32_t *>(base + o_cnt);
+  p->stage_llr = reinterpret_cast<float *>(base + o_stage);
+  p->stage_slot = reinterpret_cast<int32_t *>(base + o_stage_slot);
+  p->stage_maxit = reinterpret_cast<int32_t *>(base + o_stage_maxit);
+  for (int b = 0; b < 2; ++b) {
+    p->done_list[b] = reinterpret_cast<int32_t *>(base + o_done[b]);
+    p->pack_sym[b] = reinterpret_cast<uint16_t *>(base + o_psym[b]);
+    p->pack_ok[b] = reinterpret_cast<uint8_t *>(base + o_pok[b]);
+    p->pack_iter[b] = reinterpret_cast<int32_t *>(base + o_piter[b]);
+  }
+  // the pool owns its memory from here on: free_pool releases whatever was made
+  Pool *raw = p.get();
   srv->used += p->bytes;
-  *out = p.get();
   srv->pools[c] = std::move(p);
+  const size_t llr_bytes = (size_t)S * c->N * c->m * 4;
+  int st = check_cuda(cudaMemset(raw->cnt, 0, 32), "cudaMemset");
+  if (!st) st = check_cuda(cudaStreamCreateWithFlags(&raw->stream, cudaStreamNonBlocking), "stream");
+  if (!st)
+    st = check_cuda(cudaStreamCreateWithFlags(&raw->copy_stream, cudaStreamNonBlocking), "stream");
+  for (int b = 0; b < 2 && !st; ++b) {
+    st = check_cuda(cudaEventCreateWithFlags(&raw->round_done[b], cudaEventDisableTiming), "event");
+    if (!st) st = check_cuda(cudaMallocHost(&raw->h_llr[b], llr_bytes), "pinned");
+    if (!st) st = check_cuda(cudaMallocHost(&raw->h_slot[b], (size_t)S * 4), "pinned");
+    if (!st) st = check_cuda(cudaMallocHost(&raw->h_maxit[b], (size_t)S * 4), "pinned");
+    if (!st) st = check_cuda(cudaMallocHost(&raw->h_cnt[b], 16), "pinned");
+  }
+  if (!st) st = check_cuda(cudaMallocHost(&raw->h_done, (size_t)S * 4), "pinned");
+  if (!st) st = check_cuda(cudaMallocHost(&raw->h_sym, (size_t)S * c->N * 2), "pinned");
+  if (!st) st = check_cuda(cudaMallocHost(&raw->h_ok, (size_t)S), "pinned");
+  if (!st) st = check_cuda(cudaMallocHost(&raw->h_iters, (size_t)S * 4), "pinned");
+  if (st) {
+    free_pool(raw);
+    srv->used -= raw->bytes;
+    srv->pools.erase(c);
+    return st;
+  }
+  for (int s = raw->S - 1; s >= 0; --s) raw->free_slots.push_back(s);
+  *out = raw;
   return NBFD_OK;
-}
-
-void free_pool(Pool *p) {
-  if (p->stream) cudaStreamSynchronize(p->stream);
-  if (p->block) cudaFree(p->block);
-  if (p->stream) cudaStreamDestroy(p->stream);
-  cudaFreeHost(p->h_llr);
-  cudaFreeHost(p->h_sym);
-  cudaFreeHost(p->h_io);
-  cudaFreeHost(p->h_small);
-  cudaFreeHost(p->h_maxit);
-  cudaFreeHost(p->h_iters);
-  cudaFreeHost(p->h_ok);
 }
 
 cudaError_t launch_init_slots(const nbfd_code *c, const float *llr, float *v2c,
@@ -348,134 +408,220 @@ cudaError_t launch_init_slots(const nbfd_code *c, const float *llr, float *v2c,
   return cudaGetLastError();
 }
 
-// One round for one pool: admit from its queue, iterate, stop test; enqueued on the pool stream.
-// Returns the number of newly admitted frames (their tickets move to in_flight).
-int round_issue(nbfd_server *srv, Pool *p, std::deque<Request> &admit) {
+// Charges the time since the previous lap to one worker phase.
+struct PhaseClock {
+  nbfd_server *srv;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void lap(Phase ph) {
+    const auto n = std::chrono::steady_clock::now();
+    srv->phase_ns[ph].fetch_add(std::chrono::duration_cast<std::chrono::nanoseconds>(n - t).count(),
+                                std::memory_order_relaxed);
+    t = n;
+  }
+};
+
+// Issues one round of pool p on its stream: the n_new admissions staged in the host buffers of
+// parity p->par, one decoding iteration over the active list, the serving stop test and the
+// packing of the done slots. n_bound >= the active list's length after admission (it sizes grids
+// only: every kernel reads the length on the device).
+void round_issue(nbfd_server *srv, Pool *p, int n_new, int n_bound) {
   const nbfd_code *c = p->code;
   cudaStream_t s = p->stream;
-  const int n_new = static_cast<int>(admit.size());
-  int32_t *cur = p->lists[p->cur];
+  const int b = p->par;
+  int32_t *cur = p->lists[p->cur], *cur_n = p->cnt + kCntActive + p->cur;
+  int32_t *next = p->lists[p->cur ^ 1], *next_n = p->cnt + kCntActive + (p->cur ^ 1);
+  int32_t *done_n = p->cnt + kCntDone + b;
+  cudaError_t e = cudaSuccess;
   if (n_new > 0) {
     const size_t per = (size_t)c->N * c->m;
-    for (int i = 0; i < n_new; ++i) {
-      const int slot = p->free_slots.back();
-      p->free_slots.pop_back();
-      Request &r = admit[i];
-      memcpy(p->h_llr + (size_t)i * per, r.llr.data(), per * 4);
-      p->h_io[i] = slot;
-      p->h_maxit[i] = r.max_iter;
-      p->in_flight[slot] = std::move(r);
-    }
-    cudaMemcpyAsync(p->stage_llr, p->h_llr, (size_t)n_new * per * 4, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(p->stage_slot, p->h_io, (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(p->stage_maxit, p->h_maxit, (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
+    p->h_cnt[b][0] = n_new;
+    cudaMemcpyAsync(p->stage_llr, p->h_llr[b], (size_t)n_new * per * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->stage_slot, p->h_slot[b], (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->stage_maxit, p->h_maxit[b], (size_t)n_new * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->cnt + kCntNew, p->h_cnt[b], 4, cudaMemcpyHostToDevice, s);
     const int g = n_new < sm_count() * 8 ? n_new : sm_count() * 8;
     k_admit<<<g, 128, 0, s>>>(p->stage_llr, p->stage_slot, p->stage_maxit, n_new,
                               static_cast<int>(per), p->llr, p->iter, p->maxit);
-    // new slots appended to the active list
-    cudaMemcpyAsync(cur + p->active, p->stage_slot, (size_t)n_new * 4, cudaMemcpyDeviceToDevice, s);
-    p->h_small[0] = p->active + n_new;
-    p->h_small[1] = n_new;
-    cudaMemcpyAsync(p->cnt + p->cur, &p->h_small[0], 4, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(p->cnt + 3, &p->h_small[1], 4, cudaMemcpyHostToDevice, s);
-    launch_init_slots(c, p->llr, p->v2c, cur + p->active, p->cnt + 3, n_new, s);
+    k_append<<<1, 256, 0, s>>>(p->stage_slot, n_new, cur, cur_n);
+    e = launch_init_slots(c, p->llr, p->v2c, p->stage_slot, p->cnt + kCntNew, n_new, s);
   }
-  const int total = p->active + n_new;
-  if (total == 0) return n_new;
-  cudaMemsetAsync(p->cnt + (p->cur ^ 1), 0, 4, s);
-  cudaMemsetAsync(p->cnt + 2, 0, 4, s);
+  cudaMemsetAsync(next_n, 0, 4, s);
+  cudaMemsetAsync(done_n, 0, 4, s);
   FrameSet fs;
   fs.list = cur;
-  fs.count = p->cnt + p->cur;
-  fs.n_static = total;
-  cudaError_t e = launch_check(c, fs, p->v2c, p->c2v, s, p->cnt + 4);
-  if (e == cudaSuccess) e = launch_var(c, fs, srv->form, p->llr, p->c2v, p->v2c, p->sym, p->fsyn, s, p->cnt + 4);
+  fs.count = cur_n;
+  fs.n_static = n_bound;
+  if (e == cudaSuccess) e = launch_check(c, fs, p->v2c, p->c2v, s, p->cnt + kCntErr);
+  if (e == cudaSuccess)
+    e = launch_var(c, fs, srv->form, p->llr, p->c2v, p->v2c, p->sym, p->fsyn, s, p->cnt + kCntErr);
   if (e == cudaSuccess) {
-    int grid = total < sm_count() * 16 ? total : sm_count() * 16;
-    k_stop_serve<<<grid, 128, 0, s>>>(cur, p->cnt + p->cur, p->sym, p->fsyn, c->d_edge_var,
-                                      c->d_edge_h, c->d_gf_exp, c->d_gf_log, c->q, c->N, c->M,
-                                      c->k, c->E, p->iter, p->maxit, p->ok, p->lists[p->cur ^ 1],
-                                      p->cnt + (p->cur ^ 1), p->done_list, p->cnt + 2);
+    const int grid = n_bound < sm_count() * 16 ? n_bound : sm_count() * 16;
+    k_stop_serve<<<grid, 128, 0, s>>>(cur, cur_n, p->sym, p->fsyn, c->d_edge_var, c->d_edge_h,
+                                      c->d_gf_exp, c->d_gf_log, c->q, c->N, c->M, c->k, c->E,
+                                      p->iter, p->maxit, p->ok, next, next_n, p->done_list[b],
+                                      done_n);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) {
+  if (e == cudaSuccess) {
+    const int g = n_bound < sm_count() * 8 ? n_bound : sm_count() * 8;
+    k_gather_done<<<g, 128, 0, s>>>(p->done_list[b], done_n, p->sym, p->ok, p->iter, c->N,
+                                    p->pack_sym[b], p->pack_ok[b], p->pack_iter[b]);
+    e = cudaGetLastError();
+  }
+  cudaMemcpyAsync(&p->h_cnt[b][1], next_n, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&p->h_cnt[b][2], done_n, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&p->h_cnt[b][3], p->cnt + kCntErr, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventRecord(p->round_done[b], s);
+  if (e != cudaSuccess) {  // the server stops; this round is never retired
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->error = check_cuda(e, "serving kernels");
+    return;
   }
-  {
-    const int g = total < sm_count() * 8 ? total : sm_count() * 8;
-    k_gather_done<<<g, 128, 0, s>>>(p->done_list, p->cnt + 2, p->sym, p->ok, p->iter, c->N,
-                                    p->pack_sym, p->pack_ok, p->pack_iter);
-  }
-  // counts back: [active next, done]
-  cudaMemcpyAsync(&p->h_small[2], p->cnt + (p->cur ^ 1), 4, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&p->h_small[3], p->cnt + 2, 4, cudaMemcpyDeviceToHost, s);
-  return n_new;
+  p->issued.push_back(b);
+  p->cur ^= 1;
+  p->par ^= 1;
 }
 
+// Waits for the oldest issued round of pool p, copies its done slots' results back on the copy
+// stream (the round after it keeps the device busy meanwhile) and completes their tickets.
+void round_retire(nbfd_server *srv, Pool *p, PhaseClock &clk) {
+  const int b = p->issued.front();
+  p->issued.pop_front();
+  const nbfd_code *c = p->code;
+  cudaError_t e = cudaEventSynchronize(p->round_done[b]);
+  clk.lap(kWait);
+  const int n_done = p->h_cnt[b][2];
+  int st = check_cuda(e, "serving round");
+  if (!st && p->h_cnt[b][3] != 0)
+    st = set_error(NBFD_ETIMEDOUT, "a bounded wait in a serving kernel expired");
+  if (!st && (n_done < 0 || n_done > p->S))
+    st = set_error(NBFD_ECUDA, "serving round reported %d done slots", n_done);
+  if (!st && n_done > 0) {
+    cudaStream_t cs = p->copy_stream;
+    e = cudaStreamWaitEvent(cs, p->round_done[b], 0);
+    if (e == cudaSuccess) {
+      cudaMemcpyAsync(p->h_done, p->done_list[b], (size_t)n_done * 4, cudaMemcpyDeviceToHost, cs);
+      cudaMemcpyAsync(p->h_sym, p->pack_sym[b], (size_t)n_done * c->N * 2, cudaMemcpyDeviceToHost,
+                      cs);
+      cudaMemcpyAsync(p->h_ok, p->pack_ok[b], (size_t)n_done, cudaMemcpyDeviceToHost, cs);
+      cudaMemcpyAsync(p->h_iters, p->pack_iter[b], (size_t)n_done * 4, cudaMemcpyDeviceToHost, cs);
+      e = cudaStreamSynchronize(cs);
+    }
+    st = check_cuda(e, "serving result copy");
+  }
+  if (st) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (!srv->error) srv->error = st;
+    clk.lap(kRetire);
+    return;
+  }
+  // results are built outside the lock; only this thread changes in_flight
+  const double t = now_s();
+  struct Done {
+    int slot;
+    uint64_t ticket;
+    Result r;
+  };
+  std::vector<Done> out;
+  out.reserve(n_done);
+  for (int i = 0; i < n_done; ++i) {
+    const int slot = p->h_done[i];
+    auto it = p->in_flight.find(slot);
+    if (it == p->in_flight.end()) continue;
+    Done d;
+    d.slot = slot;
+    d.ticket = it->second.ticket;
+    d.r.sym.assign(p->h_sym + (size_t)i * c->N, p->h_sym + (size_t)(i + 1) * c->N);
+    d.r.ok = p->h_ok[i];
+    d.r.iters = p->h_iters[i];
+    d.r.latency = t - it->second.t_submit;
+    out.push_back(std::move(d));
+  }
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (Done &d : out) {
+      srv->done[d.ticket] = std::move(d.r);
+      srv->done_order.push_back(d.ticket);
+      srv->pending.erase(d.ticket);
+      p->in_flight.erase(d.slot);
+      p->free_slots.push_back(d.slot);
+    }
+    ++srv->rounds;
+  }
+  srv->cv.notify_all();
+  clk.lap(kRetire);
+}
+
+// The worker keeps up to two rounds per pool on the device: after issuing round r it retires
+// round r-1, then admits and stages round r+1 while round r runs.
 void worker_main(nbfd_server *srv) {
   cudaSetDevice(srv->device);
+  struct Work {
+    Pool *p;
+    std::vector<int> slots;  // admitted this round
+    int bound;               // frames in flight after admission
+  };
+  PhaseClock clk{srv};
   while (true) {
-    // 1. take admissions (under the lock)
-    std::vector<std::pair<Pool *, std::deque<Request>>> work;
+    std::vector<Work> work;
+    std::vector<Pool *> live;  // pools with rounds issued or about to be
     {
       std::unique_lock<std::mutex> lk(srv->mu);
-      auto busy = [&]() {
-        for (auto &kv : srv->pools)
-          if (kv.second->active > 0 || !kv.second->queue.empty()) return true;
+      auto has = [&](bool want_issued) {
+        for (auto &kv : srv->pools) {
+          const Pool *p = kv.second.get();
+          if (want_issued ? !p->issued.empty()
+                          : !p->in_flight.empty() || (!p->queue.empty() && !p->free_slots.empty()))
+            return true;
+        }
         return false;
       };
-      srv->cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return srv->stop || busy(); });
+      if (!has(true))
+        srv->cv.wait_for(lk, std::chrono::milliseconds(20),
+                         [&] { return srv->stop || srv->error || has(false); });
+      clk.lap(kIdle);
       if (srv->stop) break;
+      if (srv->error) {  // no new rounds after a failure; callers see the error
+        srv->cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return srv->stop; });
+        continue;
+      }
       for (auto &kv : srv->pools) {
         Pool *p = kv.second.get();
-        std::deque<Request> admit;
-        while (!p->queue.empty() && !p->free_slots.empty() &&
-               admit.size() < p->free_slots.size()) {
-          admit.push_back(std::move(p->queue.front()));
+        Work w{p, {}, 0};
+        while (!p->queue.empty() && !p->free_slots.empty()) {
+          const int slot = p->free_slots.back();
+          p->free_slots.pop_back();
+          p->in_flight.emplace(slot, std::move(p->queue.front()));
           p->queue.pop_front();
+          w.slots.push_back(slot);
         }
-        if (p->active > 0 || !admit.empty()) work.emplace_back(p, std::move(admit));
+        w.bound = static_cast<int>(p->in_flight.size());
+        if (w.bound > 0 || !p->issued.empty()) live.push_back(p);
+        if (w.bound > 0) work.push_back(std::move(w));
       }
     }
-    if (work.empty()) continue;
-    // 2. issue one round per pool (pools overlap on their own streams)
-    for (auto &w : work) round_issue(srv, w.first, w.second);
-    // 3. retire
-    for (auto &w : work) {
-      Pool *p = w.first;
-      cudaStreamSynchronize(p->stream);
-      const int n_next = p->h_small[2], n_done = p->h_small[3];
-      const nbfd_code *c = p->code;
-      if (n_done) {
-        cudaMemcpyAsync(p->h_io, p->done_list, (size_t)n_done * 4, cudaMemcpyDeviceToHost, p->stream);
-        cudaMemcpyAsync(p->h_sym, p->pack_sym, (size_t)n_done * c->N * 2, cudaMemcpyDeviceToHost, p->stream);
-        cudaMemcpyAsync(p->h_ok, p->pack_ok, (size_t)n_done, cudaMemcpyDeviceToHost, p->stream);
-        cudaMemcpyAsync(p->h_iters, p->pack_iter, (size_t)n_done * 4, cudaMemcpyDeviceToHost, p->stream);
-        cudaStreamSynchronize(p->stream);
+    // stage and issue: this host work overlaps the rounds already on the device
+    for (Work &w : work) {
+      Pool *p = w.p;
+      const int b = p->par;
+      const size_t per = (size_t)p->code->N * p->code->m;
+      const int n_new = static_cast<int>(w.slots.size());
+      for (int i = 0; i < n_new; ++i) {
+        const Request &r = p->in_flight.at(w.slots[i]);
+        memcpy(p->h_llr[b] + (size_t)i * per, r.llr.data(), per * 4);
+        p->h_slot[b][i] = w.slots[i];
+        p->h_maxit[b][i] = r.max_iter;
       }
-      const double t = now_s();
-      std::lock_guard<std::mutex> lk(srv->mu);
-      for (int i = 0; i < n_done; ++i) {
-        const int slot = p->h_io[i];
-        auto it = p->in_flight.find(slot);
-        if (it == p->in_flight.end()) continue;
-        Result r;
-        r.sym.assign(p->h_sym + (size_t)i * c->N, p->h_sym + (size_t)i * c->N + c->N);
-        r.ok = p->h_ok[i];
-        r.iters = p->h_iters[i];
-        r.latency = t - it->second.t_submit;
-        srv->done[it->second.ticket] = std::move(r);
-        srv->done_order.push_back(it->second.ticket);
-        srv->pending.erase(it->second.ticket);
-        p->in_flight.erase(it);
-        p->free_slots.push_back(slot);
-      }
-      p->active = n_next;
-      p->cur ^= 1;
-      ++srv->rounds;
+      clk.lap(kAdmit);
+      round_issue(srv, p, n_new, w.bound);
+      clk.lap(kIssue);
     }
-    srv->cv.notify_all();
+    // retire all but the round just issued
+    for (Pool *p : live) {
+      bool issued_now = false;
+      for (const Work &w : work) issued_now |= w.p == p;
+      while (p->issued.size() > (issued_now ? 1u : 0u)) round_retire(srv, p, clk);
+    }
   }
 }
 
@@ -517,16 +663,17 @@ extern "C" int nbfd_srv_submit(nbfd_server *srv, const nbfd_code *code, const fl
   if (max_iter < 1) return set_error(NBFD_EINVAL, "max_iter must be >= 1");
   if (!form_supported(srv->form, code->m))
     return set_error(NBFD_ENOTSUP, "the server's form does not support m = %d", code->m);
+  Request r;  // copied before the lock is taken: the worker shares it
+  r.t_submit = now_s();
+  r.llr.assign(llr_host, llr_host + (size_t)code->N * code->m);
+  r.max_iter = max_iter;
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->error) return set_error(srv->error, "the server stopped after an error");
   Pool *p = nullptr;
   if (int st = make_pool(srv, code, &p)) return st;
-  if (p->queue.size() >= srv->queue_limit) return set_error(NBFD_EBUSY, "request queue full");
-  Request r;
+  if (p->queue.size() + p->reserved >= srv->queue_limit)
+    return set_error(NBFD_EBUSY, "request queue full");
   r.ticket = srv->next_ticket++;
-  r.llr.assign(llr_host, llr_host + (size_t)code->N * code->m);
-  r.max_iter = max_iter;
-  r.t_submit = now_s();
   *ticket = r.ticket;
   srv->pending[r.ticket] = 1;
   p->queue.push_back(std::move(r));
@@ -563,24 +710,44 @@ extern "C" int nbfd_srv_submit_many(nbfd_server *srv, const nbfd_code *code, int
   if (max_iter < 1) return set_error(NBFD_EINVAL, "max_iter must be >= 1");
   if (!form_supported(srv->form, code->m))
     return set_error(NBFD_ENOTSUP, "the server's form does not support m = %d", code->m);
-  std::lock_guard<std::mutex> lk(srv->mu);
-  if (srv->error) return set_error(srv->error, "the server stopped after an error");
-  Pool *p = nullptr;
-  if (int st = make_pool(srv, code, &p)) return st;
-  if (p->queue.size() + (size_t)n > srv->queue_limit) return set_error(NBFD_EBUSY, "request queue full");
   const size_t per = (size_t)code->N * code->m;
   const double t = now_s();
-  for (int i = 0; i < n; ++i) {
-    Request r;
-    r.ticket = srv->next_ticket++;
-    r.llr.assign(llr_host + per * i, llr_host + per * (i + 1));
-    r.max_iter = max_iter;
-    r.t_submit = arrival ? arrival[i] : t;
-    tickets[i] = r.ticket;
-    srv->pending[r.ticket] = 1;
-    p->queue.push_back(std::move(r));
+  Pool *p = nullptr;
+  {
+    // tickets and queue room are taken for all n frames at once, in arrival order
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->error) return set_error(srv->error, "the server stopped after an error");
+    if (int st = make_pool(srv, code, &p)) return st;
+    if (p->queue.size() + p->reserved + (size_t)n > srv->queue_limit)
+      return set_error(NBFD_EBUSY, "request queue full");
+    p->reserved += (size_t)n;
+    for (int i = 0; i < n; ++i) {
+      tickets[i] = srv->next_ticket++;
+      srv->pending[tickets[i]] = 1;
+    }
   }
-  srv->cv.notify_all();
+  // the frames are copied and queued in chunks, outside the lock, so that the worker starts
+  // on the first chunk while the rest is copied
+  constexpr int kChunk = 256;
+  std::vector<Request> reqs;
+  for (int i0 = 0; i0 < n; i0 += kChunk) {
+    const int i1 = n - i0 < kChunk ? n : i0 + kChunk;
+    reqs.clear();
+    reqs.resize(i1 - i0);
+    for (int i = i0; i < i1; ++i) {
+      Request &r = reqs[i - i0];
+      r.ticket = tickets[i];
+      r.llr.assign(llr_host + per * i, llr_host + per * (i + 1));
+      r.max_iter = max_iter;
+      r.t_submit = arrival ? arrival[i] : t;
+    }
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      for (Request &r : reqs) p->queue.push_back(std::move(r));
+      p->reserved -= reqs.size();
+    }
+    srv->cv.notify_all();
+  }
   return NBFD_OK;
 }
 
@@ -611,12 +778,29 @@ extern "C" int nbfd_srv_stats(nbfd_server *srv, long long *rounds, long long *qu
   std::lock_guard<std::mutex> lk(srv->mu);
   long long q = 0, f = 0;
   for (auto &kv : srv->pools) {
-    q += (long long)kv.second->queue.size();
+    q += (long long)(kv.second->queue.size() + kv.second->reserved);
     f += (long long)kv.second->in_flight.size();
   }
   if (rounds) *rounds = srv->rounds;
   if (queued) *queued = q;
   if (in_flight) *in_flight = f;
   if (device_bytes) *device_bytes = srv->used;
+  return NBFD_OK;
+}
+
+extern "C" int nbfd_srv_register(nbfd_server *srv, const nbfd_code *code) {
+  if (!srv || !code) return set_error(NBFD_EINVAL, "NULL argument");
+  if (!form_supported(srv->form, code->m))
+    return set_error(NBFD_ENOTSUP, "the server's form does not support m = %d", code->m);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->error) return set_error(srv->error, "the server stopped after an error");
+  Pool *p = nullptr;
+  return make_pool(srv, code, &p);
+}
+
+extern "C" int nbfd_srv_worker_times(nbfd_server *srv, double *seconds) {
+  if (!srv || !seconds) return set_error(NBFD_EINVAL, "NULL argument");
+  for (int i = 0; i < 5; ++i)
+    seconds[i] = 1e-9 * (double)srv->phase_ns[i].load(std::memory_order_relaxed);
   return NBFD_OK;
 }
