@@ -100,3 +100,36 @@ def test_serving_poll_unknown_ticket(dev):
             nb.nbfd_srv_poll(srv, 12345, 8)
     finally:
         nb.nbfd_srv_destroy(srv)
+
+
+def test_registered_pool_and_chunked_submit_many(dev):
+    """A pool created by nbfd_srv_register serves a submit_many of several copy chunks (600
+    frames, queued 256 at a time while the worker already runs); every frame equals its decoding
+    in one nbfd_decode batch, tickets come back in order, and the worker's phase times add up."""
+    c = synth.named_code("gf16_n32_k4")
+    code = nb.Code(c)
+    _, llr = synth.frames(c, 600, 1.0, batch_idx=41)
+    form = nb.FORM_FP32_FWHT
+    srv = nb.nbfd_srv_create(1 << 30, form)
+    try:
+        nb.nbfd_srv_register(srv, code.handle)
+        nb.nbfd_srv_register(srv, code.handle)  # a second registration is a no-op
+        _, _, _, dev_bytes = nb.nbfd_srv_stats(srv)
+        assert dev_bytes > 0
+        tickets = nb.nbfd_srv_submit_many(srv, code.handle, llr, 30)
+        assert np.array_equal(np.diff(tickets.astype(np.int64)), np.ones(599, np.int64))
+        res = _wait_all(srv, tickets.tolist(), {int(t): code.N for t in tickets})
+        rounds, queued, in_flight, dev_bytes2 = nb.nbfd_srv_stats(srv)
+        assert queued == 0 and in_flight == 0 and dev_bytes2 == dev_bytes and rounds > 0
+        times = nb.nbfd_srv_worker_times(srv)
+        assert set(times) == {"admission", "issue", "wait", "retire", "idle"}
+        assert min(times.values()) >= 0 and times["issue"] > 0 and times["wait"] > 0
+    finally:
+        nb.nbfd_srv_destroy(srv)
+    ref_sym, ref_ok, ref_it = nb.decode(code, torch.from_numpy(llr).to(dev), 30, form)
+    torch.cuda.synchronize()
+    ref_sym, ref_ok, ref_it = ref_sym.cpu().numpy(), ref_ok.cpu().numpy(), ref_it.cpu().numpy()
+    for i, t in enumerate(tickets.tolist()):
+        sym, ok, it, _ = res[t]
+        assert np.array_equal(sym.astype(np.int64), ref_sym[i].astype(np.int64)), i
+        assert ok == int(ref_ok[i]) and it == int(ref_it[i]), i
