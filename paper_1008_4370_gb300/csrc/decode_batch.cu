@@ -81,10 +81,14 @@ int tune_code(const nbfd_code *c, int F, int form, const float *llr, float *v2c,
       const size_t smem = 128 * 8 + (size_t)warps * stages * cpw * c->k * c->q * 4;
       if (smem > kMaxSmemPerBlock) continue;
       const int fit = static_cast<int>((228 * 1024) / (smem + 1024));
-      for (int bps : {1, 2, 3, 4, 6}) {
-        if (bps > fit) continue;
-        // shapes that cannot give every warp a tile are not worth timing twice
-        if ((long long)bps * sms * warps > tiles * 2 && bps > 1) continue;
+      // one wave (bps <= fit) and oversubscribed grids of 2, 4 and 8 waves
+      for (int bps : {1, 2, 3, 4, 6, 2 * fit, 4 * fit, 8 * fit}) {
+        const bool over = bps > 6;
+        if (!over && bps > fit) continue;
+        // shapes that cannot give every warp a tile (or, oversubscribed, four tiles) are not
+        // worth timing
+        if ((long long)bps * sms * warps * (over ? 4 : 1) > tiles * (over ? 1 : 2) && bps > 1)
+          continue;
         CheckTune ct{warps, stages, bps};
         const float ms = time_launches(s, 3, [&] {
           return launch_check(c, fs, v2c, c2v, s, nullptr, {}, ct, stores_f16(form));
@@ -100,8 +104,8 @@ int tune_code(const nbfd_code *c, int F, int form, const float *llr, float *v2c,
   best_ms = -1.0f;
   const std::vector<int> var_bps =
       (form & 0xff) == NBFD_FORM_FP32_FWHT && (c->m == 8 || var_fwht6x8_applies(c))
-          ? std::vector<int>{1, 2, 3, 4}
-                                                          : std::vector<int>{1, 2, 4, 8, 16};
+          ? std::vector<int>{1, 2, 3, 4, 8, 16, 32}
+          : std::vector<int>{1, 2, 4, 8, 16, 32};
   for (int bps : var_bps) {
     VarTune vt{bps};
     const float ms = time_launches(s, 3, [&] {

@@ -369,7 +369,7 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
   const long long total = (long long)F * c->N;
   if (f16) {  // half storage: GF(256) only, no lambda0 output
     if (c->m != 8 || lambda0) return cudaErrorNotSupported;
-    const int grid = grid_for((total + 7) / 8, 8);
+    const int grid = grid_for((total + 7) / 8, 8 * oversubscribed_waves(total, 64LL * sm_count()));
     k_init<8, __half><<<grid, 256, 0, s>>>(llr, nullptr, reinterpret_cast<__half *>(v2c),
                                            c->d_var_edges, c->N, c->E, F, list_out, count_out);
     return cudaGetLastError();
@@ -377,7 +377,8 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
 #define NBFD_INIT(MB)                                                                        \
   {                                                                                          \
     using CL = ChannelLayout<MB>;                                                            \
-    const int grid = grid_for((total + 8 * CL::VPW - 1) / (8 * CL::VPW), 8);                 \
+    const int grid = grid_for((total + 8 * CL::VPW - 1) / (8 * CL::VPW),                     \
+                              8 * oversubscribed_waves(total / CL::VPW, 64LL * sm_count()));  \
     k_init<MB, float><<<grid, 256, 0, s>>>(llr, lambda0, v2c, c->d_var_edges, c->N, c->E, F, \
                                            list_out, count_out);                             \
   }

@@ -229,13 +229,15 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
   const int warps =
       tune.warps > 0 ? tune.warps : (k <= 4 ? 8 : (k <= 8 ? 4 : (k <= 16 ? 2 : 1)));
   const size_t smem = 128 * 8 + (size_t)warps * S * cpw * k * Q * wb;
-  // default: as many blocks per SM as shared memory holds (at least 2, at most 8)
-  int fill = static_cast<int>((228 * 1024) / (smem + 1024));
-  fill = fill < 2 ? 2 : (fill > 8 ? 8 : fill);
-  const int per_sm = tune.blocks_per_sm > 0 ? tune.blocks_per_sm : fill;
   if (warps > 8 || S < 3 || S > 8 || smem > kMaxSmemPerBlock) return cudaErrorInvalidValue;
   const long long total = (long long)fs.n_static * c->M;
   const long long n_tiles = (total + cpw - 1) / cpw;
+  // default: waves of as many blocks per SM as shared memory holds (at least 2, at most 8)
+  int fill = static_cast<int>((228 * 1024) / (smem + 1024));
+  fill = fill < 2 ? 2 : (fill > 8 ? 8 : fill);
+  const int per_sm = tune.blocks_per_sm > 0
+                         ? tune.blocks_per_sm
+                         : fill * oversubscribed_waves(n_tiles, (long long)sm_count() * fill * warps);
   long long grid = (long long)sm_count() * per_sm;
   const long long need = (n_tiles + warps - 1) / warps;
   if (grid > need) grid = need;

@@ -372,7 +372,9 @@ cudaError_t launch_var_fwht6x8(const nbfd_code *c, FrameSet fs, const float *llr
   const long long units = (long long)fs.n_static * c->N / 8;
   long long grid = (units + kX8Warps - 1) / kX8Warps;
   const int per_sm =
-      tune.blocks_per_sm > 0 && tune.blocks_per_sm < kX8MinBlocks ? tune.blocks_per_sm : kX8MinBlocks;
+      tune.blocks_per_sm > 0
+          ? tune.blocks_per_sm
+          : kX8MinBlocks * oversubscribed_waves(units, (long long)sm_count() * kX8MinBlocks * kX8Warps);
   const long long cap = (long long)sm_count() * per_sm;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;

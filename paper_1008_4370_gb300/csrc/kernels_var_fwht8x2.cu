@@ -415,7 +415,9 @@ cudaError_t launch_var_fwht8x2(const nbfd_code *c, FrameSet fs, const float *llr
   const long long units = ((long long)fs.n_static * c->N + 1) / 2;
   long long g = (units + kX2Warps - 1) / kX2Warps;
   const int per_sm =
-      tune.blocks_per_sm > 0 && tune.blocks_per_sm < kX2MinBlocks ? tune.blocks_per_sm : kX2MinBlocks;
+      tune.blocks_per_sm > 0
+          ? tune.blocks_per_sm
+          : kX2MinBlocks * oversubscribed_waves(units, (long long)sm_count() * kX2MinBlocks * kX2Warps);
   const long long cap = (long long)sm_count() * per_sm;
   if (g > cap) g = cap;
   if (g < 1) g = 1;

@@ -53,6 +53,16 @@ struct VarTune {
   int blocks_per_sm = 0;  // grid cap in blocks per SM
 };
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;
+// Waves of resident blocks for a grid-stride kernel with `work` items over `warps_per_wave`
+// warps: one wave leaves the warps' finishing times uneven (memory bandwidth is not shared
+// evenly), so the grid is oversubscribed -- up to 8 waves, the block scheduler then evening out
+// the load -- as long as every warp still gets about a dozen items to amortise its pipeline fill.
+inline int oversubscribed_waves(long long work, long long warps_per_wave) {
+  constexpr long long kItemsPerWarp = 12, kMaxWaves = 8;
+  if (warps_per_wave < 1) return 1;
+  const long long w = work / (warps_per_wave * kItemsPerWarp);
+  return static_cast<int>(w < 1 ? 1 : (w > kMaxWaves ? kMaxWaves : w));
+}
 // Launch shapes cached by the autotuner for (device, code shape, n_frames, form), if any.
 bool tune_lookup(const nbfd_code *c, int F, int form, CheckTune *ct, VarTune *vt);
 
