@@ -348,12 +348,13 @@ void nbfd_srv_destroy(nbfd_server *srv);
 #define NBFD_KERNEL_CHECK 1
 #define NBFD_KERNEL_VAR 2
 #define NBFD_KERNEL_SYNDROME 3
-#define NBFD_KERNEL_COUNT 4
+#define NBFD_KERNEL_TAIL 4 /* the remaining iterations of the last few frames, one launch */
+#define NBFD_KERNEL_COUNT 5
 
 /* Time the kernels whose bit (1 << NBFD_KERNEL_*) is set in kernel_mask (0 disables; NBFD_PROF_ALL
- * times all four) for the calling process; resets the totals. Each timed launch adds two event
+ * times all five) for the calling process; resets the totals. Each timed launch adds two event
  * records to the stream. */
-#define NBFD_PROF_ALL 0xF
+#define NBFD_PROF_ALL 0x1F
 int nbfd_prof_enable(int kernel_mask);
 /* Totals since the last enable: device milliseconds, launches, and frame-units (the sum over
  * launches of the number of frames the launch processed). Any out pointer may be NULL. */

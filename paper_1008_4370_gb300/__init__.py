@@ -35,7 +35,7 @@ FORM_FP32_TC = 4
 DECIDE_SYMBOL = 0x100  # OR into a form: symbol-MAP tentative decisions
 SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT, FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)
 TC_FORMS = (FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)  # need m = 8
-KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME = 0, 1, 2, 3
+KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME, KERNEL_TAIL = 0, 1, 2, 3, 4
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libnbfd.so")
@@ -361,7 +361,7 @@ def nbfd_srv_destroy(srv):
 
 
 def nbfd_prof_enable(kernel_mask: int):
-    """Time the kernels whose bit (1 << KERNEL_*) is set; 0 disables, 0xF times all."""
+    """Time the kernels whose bit (1 << KERNEL_*) is set; 0 disables, 0x1F times all."""
     _check(lib().nbfd_prof_enable(int(kernel_mask)))
 
 

@@ -247,10 +247,32 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
     // the last count it read, an upper bound since counts only shrink.
     // Once few frames are left (the iterations of the frames that do not converge), launches are
     // short and a host round trip costs as much as several iterations: read the count less often.
+    // Once the frames left fit the tail kernel's resident clusters, one launch runs all their
+    // remaining iterations (one thread-block cluster per frame); until then the count is read
+    // every 4 iterations, so that the switch comes early.
     long long active = F;
     int it = 1;
+    const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
+    int tail_ctas = 0;
+    const long long tail_max =
+        (form & 0xff) == NBFD_FORM_FP32_FWHT && !f16 ? tail_clusters(c, symbol, &tail_ctas) : 0;
     while (st == NBFD_OK && it <= max_iter && active > 0) {
-      const int sync_every = active * 16 <= F ? 16 : 4;
+      if (active <= tail_max) {
+        FrameSet fs;
+        fs.list = w.list[it & 1];
+        fs.count = w.count + it;
+        fs.n_static = static_cast<int>(active);
+        tm.begin(NBFD_KERNEL_TAIL, it, s);
+        if ((st = check_cuda(launch_tail_x2(c, fs, llr, w.v2c, w.c2v, symbols, w.fsyn, it,
+                                            max_iter, ok, iters, w.stats, s, symbol),
+                             "tail kernel")))
+          break;
+        tm.end(s);
+        if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
+        active = 0;
+        break;
+      }
+      const int sync_every = active * 16 <= F && tail_max == 0 ? 16 : 4;
       const int last = it + sync_every - 1 < max_iter ? it + sync_every - 1 : max_iter;
       for (; it <= last; ++it) {
         FrameSet fs;

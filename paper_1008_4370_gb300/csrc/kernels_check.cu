@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "bulk_copy.cuh"
+#include "check_math.cuh"
 #include "device_common.cuh"
 #include "nbfd_internal.h"
 
@@ -144,62 +145,7 @@ __global__ void __launch_bounds__(256)
     if (item < total) {
       const int c = static_cast<int>(item - div_m(item, M, narrow) * M);
       W *s = stages + (size_t)b * tile_floats + (size_t)ci * k * Q;
-      // index maps of the k edges at this lane's EPL entries
-      uint32_t pw[KMAX][(EPL + 3) / 4];
-#pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        if (e < k) {
-          const int h = __ldg(edge_h + (size_t)c * k + e);
-          const uint8_t *row = perm + h * Q + z0;
-          if constexpr (EPL == 8) {
-            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row));
-            pw[e][0] = w.x;
-            pw[e][1] = w.y;
-          } else if constexpr (EPL == 4) {
-            pw[e][0] = __ldg(reinterpret_cast<const uint32_t *>(row));
-          } else {
-            uint32_t w = 0;
-#pragma unroll
-            for (int jj = 0; jj < EPL; ++jj) w |= (uint32_t)__ldg(row + jj) << (8 * jj);
-            pw[e][0] = w;
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < EPL; ++j) {
-        float mag[KMAX];
-        uint32_t sg[KMAX];
-        int pos[KMAX];
-        uint32_t sx = 0;
-#pragma unroll
-        for (int e = 0; e < KMAX; ++e) {
-          if (e < k) {
-            pos[e] = (pw[e][j >> 2] >> (8 * (j & 3))) & 0xff;
-            const float x = msg_load<W>(s[e * Q + pos[e]]);
-            mag[e] = fabsf(x);
-            sg[e] = __float_as_uint(x) & 0x80000000u;
-            sx ^= sg[e];
-          }
-        }
-        float suf[KMAX];
-        float run = 0.0f;
-#pragma unroll
-        for (int e = KMAX - 1; e >= 0; --e) {
-          if (e < k) {
-            suf[e] = run;
-            run += mag[e];
-          }
-        }
-        float pre = 0.0f;
-#pragma unroll
-        for (int e = 0; e < KMAX; ++e) {
-          if (e < k) {
-            const float o = pre + suf[e];
-            pre += mag[e];
-            s[e * Q + pos[e]] = msg_store<W>(__uint_as_float(__float_as_uint(o) | (sx ^ sg[e])));
-          }
-        }
-      }
+      check_lane_inplace<Q, EPL, KMAX, W>(s, c, k, z0, edge_h, perm);
     }
     fence_proxy_async_smem();
     __syncwarp();

@@ -23,9 +23,15 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "bulk_copy.cuh"
+#include "check_math.cuh"
 #include "device_common.cuh"
 #include "nbfd_internal.h"
 
@@ -140,6 +146,164 @@ __device__ __forceinline__ void store4(__half *p, float a, float b, float c, flo
 
 }  // namespace
 
+// One unit of the variable-node update: variable v (this half-warp, sub = lane / 16) of frame f,
+// edges e1 and e2, from its two check messages msg0 / msg1 (Gamma form, natural order, in shared
+// memory) and its 8 LLRs: writes V->C on both edges, the tentative decision and the Fourier-domain
+// syndrome words when `valid`. Warp-collective (both half-warps call it together). Shared by the
+// variable-node kernel and the cluster tail kernel, so both compute bit-identical results.
+template <bool SYMBOL, typename W>
+__device__ __forceinline__ void x2_unit(const W *msg0, const W *msg1, const float *llr8,
+                                        float2 *pbt, float2 *sbuf, float *scratch_all, int f,
+                                        int v, int e1, int e2, bool valid, W *__restrict__ v2c,
+                                        uint16_t *__restrict__ sym, uint8_t *__restrict__ fsyn,
+                                        const uint8_t *__restrict__ edge_z, int N, int E, int lane,
+                                        int sub, int l, int o0, int o1, int xl1,
+                                        unsigned half_mask) {
+  // read-out points of this lane, used at the end: round 0 lanes 0..7 alpha^i, 8..15 H_e1
+  // alpha^i; round 1 lanes 0..7 H_e2 alpha^i
+  int z0 = 0, z1 = 0;
+  if (!SYMBOL) {
+    z0 = l < 8 ? (1 << l) : __ldg(edge_z + (size_t)e1 * 8 + (l & 7));
+    z1 = l < 8 ? __ldg(edge_z + (size_t)e2 * 8 + l) : 0;
+  }
+  if (l < 8) {
+    const float Li = llr8[l];
+    const float e = expf(-fabsf(Li));
+    const float big = rcp_ftz(1.0f + e), small = e * big;
+    pbt[l] = Li >= 0.0f ? make_float2(big, small) : make_float2(small, big);
+  }
+  // both check messages in layout P0, decoded from the Gamma form
+  float2 c[16];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const float4 a = load4(&msg0[4 * l + 64 * g]);
+    const float4 d = load4(&msg1[4 * l + 64 * g]);
+    c[4 * g + 0] = make_float2(gamma_decode_ftz(a.x), gamma_decode_ftz(d.x));
+    c[4 * g + 1] = make_float2(gamma_decode_ftz(a.y), gamma_decode_ftz(d.y));
+    c[4 * g + 2] = make_float2(gamma_decode_ftz(a.z), gamma_decode_ftz(d.z));
+    c[4 * g + 3] = make_float2(gamma_decode_ftz(a.w), gamma_decode_ftz(d.w));
+  }
+  // forward transforms of the pair (q x-domain check messages), P0 -> P1
+  stages4(c);
+  transpose<true>(c, sbuf, o0, o1);
+  stages4(c);
+  // x-domain messages are probability vectors: drop the negative rounding noise
+#pragma unroll
+  for (int j = 0; j < 16; ++j) c[j] = make_float2(fmaxf(c[j].x, 0.0f), fmaxf(c[j].y, 0.0f));
+  // channel term p0(x) in P1 (lane bits x0 x1 x6 x7, register bits x2..x5), then
+  // M_v = p0 . c1x . c2x and w = (p0 . c1x, p0 . c2x) = (U of e2, U of e1) in place of c
+  float mu[16];
+  {
+    const float2 q0 = pbt[0], q1 = pbt[1], q6 = pbt[6],
+                 q7 = pbt[7];
+    const float lf = ((l & 1) ? q0.y : q0.x) * ((l & 2) ? q1.y : q1.x) *
+                     ((l & 4) ? q6.y : q6.x) * ((l & 8) ? q7.y : q7.x);
+    const float2 q2 = pbt[2], q3 = pbt[3], q4 = pbt[4],
+                 q5 = pbt[5];
+    const float a0 = lf * q2.x, a1 = lf * q2.y;
+    const float bq[4] = {a0 * q3.x, a1 * q3.x, a0 * q3.y, a1 * q3.y};
+    const float c45[4] = {q4.x * q5.x, q4.y * q5.x, q4.x * q5.y, q4.y * q5.y};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float pj = bq[j & 3] * c45[j >> 2];
+      mu[j] = pj * c[j].x * c[j].y;
+      c[j] = __fmul2_rn(make_float2(pj, pj), c[j]);
+    }
+  }
+  int best_x = 0;
+  if constexpr (SYMBOL) {
+    // symbol decision: argmax over x of the x-domain marginal (ties: lowest x)
+    float best = -1.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int x = xl1 | (j << 2);
+      if (mu[j] > best || (mu[j] == best && x < best_x)) {
+        best = mu[j];
+        best_x = x;
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const float ob = __shfl_xor_sync(kFull, best, o);
+      const int oi = __shfl_xor_sync(kFull, best_x, o);
+      if (ob > best || (ob == best && oi < best_x)) {
+        best = ob;
+        best_x = oi;
+      }
+    }
+  }
+  // inverse-direction transforms of the pair, P1 -> P0 (natural order)
+  stages4(c);
+  transpose<false>(c, sbuf, o0, o1);
+  stages4(c);
+  // normalise to U(0) = 1 (x = 0: register 0 of the half-warp's lane 0); U(0) <= 0 only by
+  // underflow: then the message is delta_0
+  const float n2 = __shfl_sync(kFull, c[0].x, lane & 16), n1 = __shfl_sync(kFull, c[0].y, lane & 16);
+  const float2 r = make_float2(n2 > 0.0f ? rcp_ftz(n2) : 0.0f, n1 > 0.0f ? rcp_ftz(n1) : 0.0f);
+  if (valid) {
+    W *d2 = v2c + ((size_t)f * E + e2) * kQ, *d1 = v2c + ((size_t)f * E + e1) * kQ;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float o2[4], o1[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 sc = __ffma2_rn(c[4 * g + i], r, make_float2(0.0f, 0.0f));  // -0 -> +0
+        o2[i] = gamma_encode_ftz(sc.x);
+        o1[i] = gamma_encode_ftz(sc.y);
+      }
+      if (g == 0 && l == 0) {
+        o2[0] = 0.0f;  // Gamma(1)
+        o1[0] = 0.0f;
+      }
+      store4(d2 + 4 * l + 64 * g, o2[0], o2[1], o2[2], o2[3]);
+      store4(d1 + 4 * l + 64 * g, o1[0], o1[1], o1[2], o1[3]);
+    }
+  }
+  if constexpr (SYMBOL) {
+    // the Fourier-domain syndrome words describe bitwise decisions: with symbol decisions they
+    // are written as 0, so that the stop test rests on the GF(2^m) syndrome alone
+    if (valid && l == 0) {
+      if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(best_x);
+      if (fsyn) {
+        fsyn[(size_t)f * E + e1] = 0;
+        fsyn[(size_t)f * E + e2] = 0;
+      }
+    }
+  } else {
+    // inverse-direction transform of M, P1 -> P0, then stored in natural order for the read-out
+    float2 mp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mp[i] = make_float2(mu[i], mu[i + 8]);
+    stages4_one(mp);
+    transpose_one_to0(mp, scratch_all, o0, o1, sub);
+    stages4_one(mp);
+    float *m_nat = reinterpret_cast<float *>(sbuf);
+    *reinterpret_cast<float4 *>(m_nat + 4 * l) = make_float4(mp[0].x, mp[1].x, mp[2].x, mp[3].x);
+    *reinterpret_cast<float4 *>(m_nat + 4 * l + 64) = make_float4(mp[4].x, mp[5].x, mp[6].x, mp[7].x);
+    *reinterpret_cast<float4 *>(m_nat + 4 * l + 128) = make_float4(mp[0].y, mp[1].y, mp[2].y, mp[3].y);
+    *reinterpret_cast<float4 *>(m_nat + 4 * l + 192) = make_float4(mp[4].y, mp[5].y, mp[6].y, mp[7].y);
+    __syncwarp();
+    // TENTATIVE: signs of M at alpha^{i-1}, H_e1 alpha^{i-1} (round 0) and H_e2 alpha^{i-1}
+    // (round 1), gathered with ballots; bit 16 sub + l belongs to this half-warp
+    const bool neg0 = m_nat[z0] < 0.0f;
+    const bool neg1 = l < 8 && m_nat[z1] < 0.0f;
+    const uint32_t bal0 = __ballot_sync(kFull, neg0), bal1 = __ballot_sync(kFull, neg1);
+    const bool flip = m_nat[0] < 0.0f;
+    if (valid && l == 0) {
+      uint32_t w0 = (bal0 & half_mask) >> (16 * sub), w1 = (bal1 & half_mask) >> (16 * sub);
+      if (flip) {
+        w0 = ~w0 & 0xffffu;
+        w1 = ~w1 & 0xffu;
+      }
+      if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(w0 & 0xffu);
+      if (fsyn) {
+        fsyn[(size_t)f * E + e1] = static_cast<uint8_t>((w0 >> 8) & 0xffu);
+        fsyn[(size_t)f * E + e2] = static_cast<uint8_t>(w1 & 0xffu);
+      }
+    }
+  }
+}
+
 template <bool SYMBOL, typename W, int WARPS, int S, int MINB>
 __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_var_fwht8x2(const float *__restrict__ llr, const W *__restrict__ c2v, W *__restrict__ v2c,
@@ -246,149 +410,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     const bool valid = item < total;
     const int4 ix = ws.idx[b][sub];
     const int f = ix.x, v = ix.y, e1 = ix.z, e2 = ix.w;
-    // read-out points of this lane, used at the end: round 0 lanes 0..7 alpha^i, 8..15 H_e1
-    // alpha^i; round 1 lanes 0..7 H_e2 alpha^i
-    int z0 = 0, z1 = 0;
-    if (!SYMBOL) {
-      z0 = l < 8 ? (1 << l) : __ldg(edge_z + (size_t)e1 * 8 + (l & 7));
-      z1 = l < 8 ? __ldg(edge_z + (size_t)e2 * 8 + l) : 0;
-    }
-    if (l < 8) {
-      const float Li = ws.llr[b][sub][l];
-      const float e = expf(-fabsf(Li));
-      const float big = rcp_ftz(1.0f + e), small = e * big;
-      ws.pbt[sub][l] = Li >= 0.0f ? make_float2(big, small) : make_float2(small, big);
-    }
-    // both check messages in layout P0, decoded from the Gamma form
-    float2 c[16];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const float4 a = load4(&ws.msg[b][sub][0][4 * l + 64 * g]);
-      const float4 d = load4(&ws.msg[b][sub][1][4 * l + 64 * g]);
-      c[4 * g + 0] = make_float2(gamma_decode_ftz(a.x), gamma_decode_ftz(d.x));
-      c[4 * g + 1] = make_float2(gamma_decode_ftz(a.y), gamma_decode_ftz(d.y));
-      c[4 * g + 2] = make_float2(gamma_decode_ftz(a.z), gamma_decode_ftz(d.z));
-      c[4 * g + 3] = make_float2(gamma_decode_ftz(a.w), gamma_decode_ftz(d.w));
-    }
-    // forward transforms of the pair (q x-domain check messages), P0 -> P1
-    stages4(c);
-    transpose<true>(c, sbuf, o0, o1);
-    stages4(c);
-    // x-domain messages are probability vectors: drop the negative rounding noise
-#pragma unroll
-    for (int j = 0; j < 16; ++j) c[j] = make_float2(fmaxf(c[j].x, 0.0f), fmaxf(c[j].y, 0.0f));
-    // channel term p0(x) in P1 (lane bits x0 x1 x6 x7, register bits x2..x5), then
-    // M_v = p0 . c1x . c2x and w = (p0 . c1x, p0 . c2x) = (U of e2, U of e1) in place of c
-    float mu[16];
-    {
-      const float2 q0 = ws.pbt[sub][0], q1 = ws.pbt[sub][1], q6 = ws.pbt[sub][6],
-                   q7 = ws.pbt[sub][7];
-      const float lf = ((l & 1) ? q0.y : q0.x) * ((l & 2) ? q1.y : q1.x) *
-                       ((l & 4) ? q6.y : q6.x) * ((l & 8) ? q7.y : q7.x);
-      const float2 q2 = ws.pbt[sub][2], q3 = ws.pbt[sub][3], q4 = ws.pbt[sub][4],
-                   q5 = ws.pbt[sub][5];
-      const float a0 = lf * q2.x, a1 = lf * q2.y;
-      const float bq[4] = {a0 * q3.x, a1 * q3.x, a0 * q3.y, a1 * q3.y};
-      const float c45[4] = {q4.x * q5.x, q4.y * q5.x, q4.x * q5.y, q4.y * q5.y};
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float pj = bq[j & 3] * c45[j >> 2];
-        mu[j] = pj * c[j].x * c[j].y;
-        c[j] = __fmul2_rn(make_float2(pj, pj), c[j]);
-      }
-    }
-    int best_x = 0;
-    if constexpr (SYMBOL) {
-      // symbol decision: argmax over x of the x-domain marginal (ties: lowest x)
-      float best = -1.0f;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int x = xl1 | (j << 2);
-        if (mu[j] > best || (mu[j] == best && x < best_x)) {
-          best = mu[j];
-          best_x = x;
-        }
-      }
-#pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
-        const float ob = __shfl_xor_sync(kFull, best, o);
-        const int oi = __shfl_xor_sync(kFull, best_x, o);
-        if (ob > best || (ob == best && oi < best_x)) {
-          best = ob;
-          best_x = oi;
-        }
-      }
-    }
-    // inverse-direction transforms of the pair, P1 -> P0 (natural order)
-    stages4(c);
-    transpose<false>(c, sbuf, o0, o1);
-    stages4(c);
-    // normalise to U(0) = 1 (x = 0: register 0 of the half-warp's lane 0); U(0) <= 0 only by
-    // underflow: then the message is delta_0
-    const float n2 = __shfl_sync(kFull, c[0].x, lane & 16), n1 = __shfl_sync(kFull, c[0].y, lane & 16);
-    const float2 r = make_float2(n2 > 0.0f ? rcp_ftz(n2) : 0.0f, n1 > 0.0f ? rcp_ftz(n1) : 0.0f);
-    if (valid) {
-      W *d2 = v2c + ((size_t)f * E + e2) * kQ, *d1 = v2c + ((size_t)f * E + e1) * kQ;
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        float o2[4], o1[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float2 sc = __ffma2_rn(c[4 * g + i], r, make_float2(0.0f, 0.0f));  // -0 -> +0
-          o2[i] = gamma_encode_ftz(sc.x);
-          o1[i] = gamma_encode_ftz(sc.y);
-        }
-        if (g == 0 && l == 0) {
-          o2[0] = 0.0f;  // Gamma(1)
-          o1[0] = 0.0f;
-        }
-        store4(d2 + 4 * l + 64 * g, o2[0], o2[1], o2[2], o2[3]);
-        store4(d1 + 4 * l + 64 * g, o1[0], o1[1], o1[2], o1[3]);
-      }
-    }
-    if constexpr (SYMBOL) {
-      // the Fourier-domain syndrome words describe bitwise decisions: with symbol decisions they
-      // are written as 0, so that the stop test rests on the GF(2^m) syndrome alone
-      if (valid && l == 0) {
-        if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(best_x);
-        if (fsyn) {
-          fsyn[(size_t)f * E + e1] = 0;
-          fsyn[(size_t)f * E + e2] = 0;
-        }
-      }
-    } else {
-      // inverse-direction transform of M, P1 -> P0, then stored in natural order for the read-out
-      float2 mp[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) mp[i] = make_float2(mu[i], mu[i + 8]);
-      stages4_one(mp);
-      transpose_one_to0(mp, reinterpret_cast<float *>(ws.scratch), o0, o1, sub);
-      stages4_one(mp);
-      float *m_nat = reinterpret_cast<float *>(sbuf);
-      *reinterpret_cast<float4 *>(m_nat + 4 * l) = make_float4(mp[0].x, mp[1].x, mp[2].x, mp[3].x);
-      *reinterpret_cast<float4 *>(m_nat + 4 * l + 64) = make_float4(mp[4].x, mp[5].x, mp[6].x, mp[7].x);
-      *reinterpret_cast<float4 *>(m_nat + 4 * l + 128) = make_float4(mp[0].y, mp[1].y, mp[2].y, mp[3].y);
-      *reinterpret_cast<float4 *>(m_nat + 4 * l + 192) = make_float4(mp[4].y, mp[5].y, mp[6].y, mp[7].y);
-      __syncwarp();
-      // TENTATIVE: signs of M at alpha^{i-1}, H_e1 alpha^{i-1} (round 0) and H_e2 alpha^{i-1}
-      // (round 1), gathered with ballots; bit 16 sub + l belongs to this half-warp
-      const bool neg0 = m_nat[z0] < 0.0f;
-      const bool neg1 = l < 8 && m_nat[z1] < 0.0f;
-      const uint32_t bal0 = __ballot_sync(kFull, neg0), bal1 = __ballot_sync(kFull, neg1);
-      const bool flip = m_nat[0] < 0.0f;
-      if (valid && l == 0) {
-        uint32_t w0 = (bal0 & half_mask) >> (16 * sub), w1 = (bal1 & half_mask) >> (16 * sub);
-        if (flip) {
-          w0 = ~w0 & 0xffffu;
-          w1 = ~w1 & 0xffu;
-        }
-        if (sym) sym[(size_t)f * N + v] = static_cast<uint16_t>(w0 & 0xffu);
-        if (fsyn) {
-          fsyn[(size_t)f * E + e1] = static_cast<uint8_t>((w0 >> 8) & 0xffu);
-          fsyn[(size_t)f * E + e2] = static_cast<uint8_t>(w1 & 0xffu);
-        }
-      }
-    }
+    x2_unit<SYMBOL, W>(ws.msg[b][sub][0], ws.msg[b][sub][1], ws.llr[b][sub], ws.pbt[sub], sbuf,
+                       reinterpret_cast<float *>(ws.scratch), f, v, e1, e2, valid, v2c, sym, fsyn,
+                       edge_z, N, E, lane, sub, l, o0, o1, xl1, half_mask);
     __syncwarp();
   }
   if (failed && lane == 0) {
@@ -435,6 +459,227 @@ cudaError_t launch_var_fwht8x2(const nbfd_code *c, FrameSet fs, const float *llr
                   : go(k_var_fwht8x2<false, __half, Wp, St, Mb>, __half());
   return symbol ? go(k_var_fwht8x2<true, float, Wp, St, Mb>, 0.0f)
                 : go(k_var_fwht8x2<false, float, Wp, St, Mb>, 0.0f);
+}
+
+// ---- the tail: one thread-block cluster per remaining frame ----------------------------------
+// Once few frames are left (those that do not converge run to max_iter), each iteration costs
+// three launches whose fixed latency far exceeds their work. k_tail_x2 runs all remaining
+// iterations of each remaining frame inside one thread-block cluster: per iteration the variable
+// node, a cluster barrier, the stop test's partial syndromes (each CTA's share of the checks,
+// sent to every CTA's shared memory) together with the next iteration's check node, and a
+// second cluster barrier, after which every CTA takes the same stop decision. Each unit of work
+// calls the arithmetic of the iteration kernels (check_lane_inplace, x2_unit), so results are
+// bit-identical. Messages written by other CTAs are read with L2-only loads. GF(256), float
+// message storage, k <= 8.
+
+namespace {
+constexpr int kTailWarps = 16;
+constexpr int kTailMaxCtas = 16;
+
+template <int KMAX>
+struct TailWarpMem {
+  union {
+    float tile[KMAX * kQ];  // check node: the k slots of one check
+    struct {
+      float msg[2][2][kQ];  // variable node: [variable][edge 1, edge 2][z]
+      float llr[2][8];
+      float2 scratch[2][kBuf];
+      float2 pbt[2][8];
+    } v;
+  };
+};
+template <int KMAX>
+constexpr size_t tail_smem() {
+  return sizeof(TailWarpMem<KMAX>) * kTailWarps;
+}
+}  // namespace
+
+template <bool SYMBOL, int KMAX>
+__global__ void __launch_bounds__(32 * kTailWarps, 1)
+    k_tail_x2(const float *__restrict__ llr, float *v2c, float *c2v, uint16_t *sym, uint8_t *fsyn,
+              const int32_t *__restrict__ var_edges, const int32_t *__restrict__ edge_var,
+              const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ edge_z,
+              const uint8_t *__restrict__ perm, const uint8_t *__restrict__ gexp,
+              const uint8_t *__restrict__ glog, int N, int M, int k, int E, FrameSet fs, int it0,
+              int max_iter, uint8_t *__restrict__ ok, int32_t *__restrict__ iters,
+              int32_t *__restrict__ stats) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t flags[kTailMaxCtas];  // per CTA of the cluster: bit 0 Fourier, bit 1 GF
+  const int rank = static_cast<int>(cluster.block_rank());
+  const int ncta = static_cast<int>(cluster.num_blocks());
+  const int slot = static_cast<int>(blockIdx.x) / ncta;
+  // the frame count is the same word for every CTA of the cluster: the whole cluster leaves
+  if (slot >= (fs.list ? __ldg(fs.count) : fs.n_static)) return;
+  const int f = fs.list ? __ldg(fs.list + slot) : slot;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane >> 4, l = lane & 15;
+  TailWarpMem<KMAX> &wm = reinterpret_cast<TailWarpMem<KMAX> *>(smem_raw)[wib];
+  const int gwarp = rank * kTailWarps + wib, nwarp = ncta * kTailWarps;
+  const int gthread = rank * blockDim.x + threadIdx.x, nthread = ncta * blockDim.x;
+  const int units = (N + 1) >> 1;
+  const size_t fE = (size_t)f * E;
+  const int o0 = ((l & 1) ? pw(2) : 0) + ((l & 2) ? pw(3) : 0) + ((l & 4) ? pw(4) : 0) +
+                 ((l & 8) ? pw(5) : 0);
+  const int o1 = ((l & 1) ? pw(0) : 0) + ((l & 2) ? pw(1) : 0) + ((l & 4) ? pw(6) : 0) +
+                 ((l & 8) ? pw(7) : 0);
+  const int xl1 = (l & 3) | ((l >> 2) & 3) << 6;
+  const unsigned half_mask = sub ? 0xffff0000u : 0x0000ffffu;
+  // CHECK TO VARIABLE: one check per warp tile, lane entries z = 8 lane .. 8 lane + 7
+  auto check_phase = [&]() {
+    for (int c = gwarp; c < M; c += nwarp) {
+      const float4 *src = reinterpret_cast<const float4 *>(v2c + (fE + (size_t)c * k) * kQ);
+      float4 *t4 = reinterpret_cast<float4 *>(wm.tile);
+      for (int i = lane; i < k * (kQ / 4); i += 32) t4[i] = __ldcg(src + i);
+      __syncwarp();
+      check_lane_inplace<kQ, 8, KMAX, float>(wm.tile, c, k, 8 * lane, edge_h, perm);
+      __syncwarp();
+      float4 *dst = reinterpret_cast<float4 *>(c2v + (fE + (size_t)c * k) * kQ);
+      for (int i = lane; i < k * (kQ / 4); i += 32) dst[i] = t4[i];
+      __syncwarp();
+    }
+  };
+  check_phase();
+  cluster.sync();
+  for (int it = it0;; ++it) {
+    // VARIABLE TO CHECK + TENTATIVE DECISION: two variables per warp unit
+    for (int u = gwarp; u < units; u += nwarp) {
+      const bool valid = 2 * u + sub < N;
+      const int v = valid ? 2 * u + sub : 2 * u;  // a stand-in computes and stores nothing
+      const int2 e = __ldg(reinterpret_cast<const int2 *>(var_edges) + v);
+      const float4 *m1 = reinterpret_cast<const float4 *>(c2v + (fE + e.x) * kQ);
+      const float4 *m2 = reinterpret_cast<const float4 *>(c2v + (fE + e.y) * kQ);
+      float4 *d1 = reinterpret_cast<float4 *>(wm.v.msg[sub][0]);
+      float4 *d2 = reinterpret_cast<float4 *>(wm.v.msg[sub][1]);
+      for (int i = l; i < kQ / 4; i += 16) {
+        d1[i] = __ldcg(m1 + i);
+        d2[i] = __ldcg(m2 + i);
+      }
+      if (l < 8) wm.v.llr[sub][l] = __ldg(llr + ((size_t)f * N + v) * 8 + l);
+      __syncwarp();
+      x2_unit<SYMBOL, float>(wm.v.msg[sub][0], wm.v.msg[sub][1], wm.v.llr[sub], wm.v.pbt[sub],
+                             wm.v.scratch[sub], reinterpret_cast<float *>(wm.v.scratch), f, v,
+                             e.x, e.y, valid, v2c, sym, fsyn, edge_z, N, E, lane, sub, l, o0, o1,
+                             xl1, half_mask);
+      __syncwarp();
+    }
+    cluster.sync();
+    // stop test, this CTA's share of the checks: Fourier-domain and GF(2^m) syndromes
+    int ffail = 0, efail = 0;
+    for (int c = gthread; c < M; c += nthread) {
+      int fsv = 0, esv = 0;
+      for (int j = 0; j < k; ++j) {
+        const int ed = c * k + j;
+        fsv ^= __ldcg(fsyn + fE + ed);
+        const int x = __ldcg(sym + (size_t)f * N + __ldg(edge_var + ed));
+        esv ^= x == 0 ? 0 : __ldg(gexp + __ldg(glog + __ldg(edge_h + ed)) + __ldg(glog + x));
+      }
+      ffail |= fsv != 0;
+      efail |= esv != 0;
+    }
+    ffail = __syncthreads_or(ffail);
+    efail = __syncthreads_or(efail);
+    if (threadIdx.x < (unsigned)ncta)
+      *cluster.map_shared_rank(&flags[rank], static_cast<int>(threadIdx.x)) =
+          (ffail ? 1u : 0u) | (efail ? 2u : 0u);
+    // the next iteration's check node does not depend on the stop decision (messages of a frame
+    // that stops are never read again)
+    if (it < max_iter) check_phase();
+    cluster.sync();
+    uint32_t all = 0;
+    for (int r = 0; r < ncta; ++r) all |= flags[r];
+    const bool ff = all & 1u, ef = (all & 2u) != 0;
+    const bool stop = (!ff && !ef) || it >= max_iter;
+    if (rank == 0 && threadIdx.x == 0) {
+      if (!ff && ef) atomicAdd(stats, 1);  // the Fourier-domain syndrome cleared, H x_hat != 0
+      if (stop) {
+        ok[f] = ef ? 0 : 1;
+        iters[f] = it;
+      }
+    }
+    if (stop) break;
+  }
+}
+
+// Clusters of the tail kernel that can be resident at once (0: the kernel cannot run), and the
+// cluster size it uses; computed once per device and shape.
+int tail_clusters(const nbfd_code *c, bool symbol, int *ctas) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, bool>, std::pair<int, int>> cache;
+  if (c->m != 8 || c->k > 8) return 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const int kmax = c->k <= 4 ? 4 : 8;
+  const auto key = std::make_tuple(dev, kmax, symbol);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *ctas = it->second.second;
+      return it->second.first;
+    }
+  }
+  auto probe = [&](auto kern, size_t smem) -> std::pair<int, int> {
+    if (ensure_smem((const void *)kern, smem) != cudaSuccess) return {0, 0};
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int n : {kTailMaxCtas, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(n);
+      cfg.blockDim = dim3(32 * kTailWarps);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = n;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)kern, &cfg) == cudaSuccess &&
+          clusters > 0)
+        return {clusters, n};
+      cudaGetLastError();  // clear a refusal of this size, try the next
+    }
+    return {0, 0};
+  };
+  std::pair<int, int> r;
+  if (kmax == 4)
+    r = symbol ? probe(k_tail_x2<true, 4>, tail_smem<4>()) : probe(k_tail_x2<false, 4>, tail_smem<4>());
+  else
+    r = symbol ? probe(k_tail_x2<true, 8>, tail_smem<8>()) : probe(k_tail_x2<false, 8>, tail_smem<8>());
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = r;
+  *ctas = r.second;
+  return r.first;
+}
+
+cudaError_t launch_tail_x2(const nbfd_code *c, FrameSet fs, const float *llr, float *v2c,
+                           float *c2v, uint16_t *sym, uint8_t *fsyn, int it0, int max_iter,
+                           uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s,
+                           bool symbol) {
+  int ctas = 0;
+  if (tail_clusters(c, symbol, &ctas) <= 0 || fs.n_static < 1) return cudaErrorNotSupported;
+  const int kmax = c->k <= 4 ? 4 : 8;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(fs.n_static * ctas);
+  cfg.blockDim = dim3(32 * kTailWarps);
+  cfg.dynamicSmemBytes = kmax == 4 ? tail_smem<4>() : tail_smem<8>();
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  auto go = [&](auto kern) {
+    return cudaLaunchKernelEx(&cfg, kern, llr, v2c, c2v, sym, fsyn, c->d_var_edges, c->d_edge_var,
+                              c->d_edge_h, c->d_edge_z, c->d_perm, c->d_gf_exp, c->d_gf_log, c->N,
+                              c->M, c->k, c->E, fs, it0, max_iter, ok, iters, stats);
+  };
+  if (kmax == 4) return symbol ? go(k_tail_x2<true, 4>) : go(k_tail_x2<false, 4>);
+  return symbol ? go(k_tail_x2<true, 8>) : go(k_tail_x2<false, 8>);
 }
 
 }  // namespace nbfd

@@ -126,6 +126,14 @@ bool var_fwht6x8_applies(const nbfd_code *c);
 cudaError_t launch_var_fwht6x8(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                                float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
                                cudaStream_t s, bool symbol, VarTune tune = {});
+// GF(256), float storage, k <= 8: all iterations it0 .. max_iter of the frames in fs, one
+// thread-block cluster per frame (see kernels_var_fwht8x2.cu). tail_clusters gives how many
+// clusters can be resident at once (0: not available) and their size in CTAs.
+int tail_clusters(const nbfd_code *c, bool symbol, int *ctas);
+cudaError_t launch_tail_x2(const nbfd_code *c, FrameSet fs, const float *llr, float *v2c,
+                           float *c2v, uint16_t *sym, uint8_t *fsyn, int it0, int max_iter,
+                           uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s,
+                           bool symbol);
 // GF(256) only: the same computation with two variables per warp, 16 entries per lane, one
 // shared-memory transpose per transform and packed f32x2 butterflies
 cudaError_t launch_var_fwht8x2(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
