@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
   const int sub = lane >> 4, l = lane & 15;
   TailWarpMem<KMAX> &wm = reinterpret_cast<TailWarpMem<KMAX> *>(smem_raw)[wib];
   const int gwarp = rank * kTailWarps + wib, nwarp = ncta * kTailWarps;
-  const int gthread = rank * blockDim.x + threadIdx.x, nthread = ncta * blockDim.x;
+  const int cper = (M + ncta - 1) / ncta;  // checks of this CTA's share of the stop test
+  const int cbeg = rank * cper, cend = M < cbeg + cper ? M : cbeg + cper;
   const int units = (N + 1) >> 1;
   const size_t fE = (size_t)f * E;
   const int o0 = ((l & 1) ? pw(2) : 0) + ((l & 2) ? pw(3) : 0) + ((l & 4) ? pw(4) : 0) +
@@ -565,27 +566,44 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
       __syncwarp();
     }
     cluster.sync();
-    // stop test, this CTA's share of the checks: Fourier-domain and GF(2^m) syndromes
+    // stop test over this CTA's share of the checks, one check per warp, lane j on edge j:
+    // Fourier-domain and GF(2^m) syndromes. The first check's loads are issued before the next
+    // iteration's check node and used after it, so that their latency overlaps its work (the
+    // check node does not depend on the stop decision: messages of a frame that stops are never
+    // read again).
     int ffail = 0, efail = 0;
-    for (int c = gthread; c < M; c += nthread) {
-      int fsv = 0, esv = 0;
-      for (int j = 0; j < k; ++j) {
-        const int ed = c * k + j;
-        fsv ^= __ldcg(fsyn + fE + ed);
-        const int x = __ldcg(sym + (size_t)f * N + __ldg(edge_var + ed));
-        esv ^= x == 0 ? 0 : __ldg(gexp + __ldg(glog + __ldg(edge_h + ed)) + __ldg(glog + x));
+    uint32_t fb = 0;
+    int xv = 0, hv = 0;
+    auto stop_load = [&](int cs) {
+      fb = 0;
+      xv = 0;
+      hv = 0;
+      if (cs < cend && lane < k) {
+        const int ed = cs * k + lane;
+        fb = __ldcg(fsyn + fE + ed);
+        xv = __ldcg(sym + (size_t)f * N + __ldg(edge_var + ed));
+        hv = __ldg(edge_h + ed);
       }
-      ffail |= fsv != 0;
-      efail |= esv != 0;
+    };
+    stop_load(cbeg + wib);
+    if (it < max_iter) check_phase();
+    for (int cs = cbeg + wib; cs < cend; cs += kTailWarps) {
+      if (cs != cbeg + wib) stop_load(cs);
+      uint32_t fx = fb;
+      int gx = xv == 0 ? 0 : __ldg(gexp + __ldg(glog + hv) + __ldg(glog + xv));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fx ^= __shfl_xor_sync(0xffffffffu, fx, o);
+        gx ^= __shfl_xor_sync(0xffffffffu, gx, o);
+      }
+      ffail |= fx != 0;
+      efail |= gx != 0;
     }
     ffail = __syncthreads_or(ffail);
     efail = __syncthreads_or(efail);
     if (threadIdx.x < (unsigned)ncta)
       *cluster.map_shared_rank(&flags[rank], static_cast<int>(threadIdx.x)) =
           (ffail ? 1u : 0u) | (efail ? 2u : 0u);
-    // the next iteration's check node does not depend on the stop decision (messages of a frame
-    // that stops are never read again)
-    if (it < max_iter) check_phase();
     cluster.sync();
     uint32_t all = 0;
     for (int r = 0; r < ncta; ++r) all |= flags[r];
