@@ -46,13 +46,13 @@ FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 #          --batches 1 --form fwht --store16-steps 0 --uneven-steps 0
 MEASURED_TRAFFIC = {
     ("var", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (272707072 + 219531008) / 256,
-        "sources": ["kernels_var_fwht8x2.cu", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "6e922641940fb11f"},
+        "bytes_per_frame": (272704768 + 218983168) / 256,
+        "sources": ["kernels_var_fwht8x2.cu", "check_math.cuh", "device_common.cuh", "bulk_copy.cuh"],
+        "sha256_16": "3ce20a16890dd27b"},
     ("check", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (268545280 + 214952704) / 256,
-        "sources": ["kernels_check.cu", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "5aa528129c08fb4b"},
+        "bytes_per_frame": (268642048 + 215022848) / 256,
+        "sources": ["kernels_check.cu", "check_math.cuh", "device_common.cuh", "bulk_copy.cuh"],
+        "sha256_16": "6c69afc96b2d0357"},
 }
 
 
