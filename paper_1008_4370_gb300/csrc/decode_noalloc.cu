@@ -109,7 +109,24 @@ extern "C" int nbfd_decode_noalloc(const nbfd_code *c, int F, const float *llr, 
                           "init kernel"))
     return st;
   int32_t active = F;  // pageable host word: the copy below completes before it returns
+  // the last few GF(256) frames: one launch for all their remaining iterations (as nbfd_decode)
+  const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
+  int tail_ctas = 0;
+  const int tail_max = (form & 0xff) == NBFD_FORM_FP32_FWHT && !stores_f16(form)
+                           ? tail_clusters(c, symbol, &tail_ctas)
+                           : 0;
   for (int it = 1; it <= max_iter && active > 0; ++it) {
+    if (active <= tail_max) {
+      FrameSet fs;
+      fs.list = w.list[it & 1];
+      fs.count = w.count + it;
+      fs.n_static = active;
+      if (int st = check_cuda(launch_tail_x2(c, fs, llr, w.v2c, w.c2v, symbols, w.fsyn, it,
+                                             max_iter, ok, iters, w.stats, s, symbol),
+                              "tail kernel"))
+        return st;
+      return check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
     FrameSet fs;
     fs.list = w.list[it & 1];
     fs.count = w.count + it;

@@ -33,12 +33,12 @@ def _outputs(F, N, dev):
             torch.full((F,), -3, dtype=torch.int32, device=dev))
 
 
-def _check_against_decode(code, llr, max_iter, dev):
+def _check_against_decode(code, llr, max_iter, dev, form=nb.FORM_FP32_DIRECT):
     F = llr.shape[0]
     x = torch.from_numpy(llr).to(dev)
-    ref_sym, ref_ok, ref_it = nb.decode(code, x, max_iter, nb.FORM_FP32_DIRECT)
+    ref_sym, ref_ok, ref_it = nb.decode(code, x, max_iter, form)
     sym, ok, it = _outputs(F, code.N, dev)
-    nb.nbfd_decode_noalloc(code.handle, F, x, max_iter, nb.FORM_FP32_DIRECT, sym, ok, it)
+    nb.nbfd_decode_noalloc(code.handle, F, x, max_iter, form, sym, ok, it)
     torch.cuda.synchronize()
     assert torch.equal(sym, ref_sym)
     assert torch.equal(ok, ref_ok)
@@ -46,21 +46,23 @@ def _check_against_decode(code, llr, max_iter, dev):
     return ok.cpu().numpy(), it.cpu().numpy()
 
 
-def test_noalloc_matches_decode_on_consecutive_calls(dev):
+@pytest.mark.parametrize("form", [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT])
+def test_noalloc_matches_decode_on_consecutive_calls(dev, form):
+    """With the FWHT form both entry points finish the last GF(256) frames in the tail kernel."""
     c = synth.named_code("gf256_n512_k4")
     code = nb.Code(c)
     enc = synth.Encoder(c)
     # first call: 24 frames (50 MiB of scratch); second call: fewer frames at another SNR, so it
     # runs on whatever the first call left in the shared array
     _, llr1 = synth.frames(c, 24, 1.5, batch_idx=51, encoder=enc)
-    ok1, it1 = _check_against_decode(code, llr1, 60, dev)
+    ok1, it1 = _check_against_decode(code, llr1, 60, dev, form)
     _, llr2 = synth.frames(c, 7, 0.75, batch_idx=52, encoder=enc)
-    ok2, it2 = _check_against_decode(code, llr2, 60, dev)
+    ok2, it2 = _check_against_decode(code, llr2, 60, dev, form)
     assert it1.min() >= 1 and it2.min() >= 1
     # and a different code and field through the same array
     t = synth.named_code("gf16_n32_k4")
     _, llr3 = synth.frames(t, 100, 2.0, zero_codeword=True)
-    _check_against_decode(nb.Code(t), llr3, 50, dev)
+    _check_against_decode(nb.Code(t), llr3, 50, dev, form)
 
 
 def test_noalloc_rejects_a_batch_larger_than_its_scratch(dev):
