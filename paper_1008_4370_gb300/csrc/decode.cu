@@ -236,26 +236,32 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       break;
     if ((st = check_cuda(cudaMemsetAsync(w.stats, 0, 64, s), "cudaMemsetAsync"))) break;
     if ((st = check_cuda(cudaMemsetAsync(ok, 0, (size_t)F, s), "cudaMemsetAsync"))) break;
-    // INITIALIZATION (+ list of iteration 1 = all frames, count[1] = F)
-    tm.begin(NBFD_KERNEL_INIT, 0, s);
-    if ((st = check_cuda(launch_init(c, F, llr, nullptr, w.v2c, w.list[1], w.count + 1, s, f16),
-                         "init kernel")))
-      break;
-    tm.end(s);
-    // The host reads the active-frame count every kSyncEvery iterations; in between it queues
-    // iterations blindly (a launch with no active frame returns at once) and sizes each grid by
-    // the last count it read, an upper bound since counts only shrink.
-    // Once few frames are left (the iterations of the frames that do not converge), launches are
-    // short and a host round trip costs as much as several iterations: read the count less often.
     // Once the frames left fit the tail kernel's resident clusters, one launch runs all their
-    // remaining iterations (one thread-block cluster per frame); until then the count is read
-    // every 4 iterations, so that the switch comes early.
-    long long active = F;
-    int it = 1;
+    // remaining iterations (one thread-block cluster per frame).
     const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
     int tail_ctas = 0;
     const long long tail_max =
         (form & 0xff) == NBFD_FORM_FP32_FWHT && !f16 ? tail_clusters(c, symbol, &tail_ctas) : 0;
+    // INITIALIZATION (+ list of iteration 1 = all frames, count[1] = F). V->C of both edges of a
+    // variable is its Lambda0: with float storage, unless the tail kernel runs from the first
+    // iteration, Lambda0 is written once per variable ([frame][variable][z], in the V->C buffer,
+    // which the first variable-node launch overwrites) and the first check launch gathers it
+    // per edge -- half the INITIALIZATION's writes (for q >= 64, where a vector is one bulk copy
+    // of at least 256 bytes).
+    const float *lambda0 = !f16 && F > tail_max && c->q >= 64 ? w.v2c : nullptr;
+    tm.begin(NBFD_KERNEL_INIT, 0, s);
+    if ((st = check_cuda(launch_init(c, F, llr, lambda0 ? w.v2c : nullptr,
+                                     lambda0 ? nullptr : w.v2c, w.list[1], w.count + 1, s, f16),
+                         "init kernel")))
+      break;
+    tm.end(s);
+    // The host reads the active-frame count every few iterations; in between it queues
+    // iterations blindly (a launch with no active frame returns at once) and sizes each grid by
+    // the last count it read, an upper bound since counts only shrink. With the tail kernel the
+    // count is read every 4 iterations, so that the switch to it comes early; without it, every
+    // 16 once few frames are left (a host round trip then costs as much as several iterations).
+    long long active = F;
+    int it = 1;
     while (st == NBFD_OK && it <= max_iter && active > 0) {
       if (active <= tail_max) {
         FrameSet fs;
@@ -280,7 +286,8 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
         fs.count = w.count + it;
         fs.n_static = static_cast<int>(active);
         tm.begin(NBFD_KERNEL_CHECK, it, s);
-        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1, {}, check_tune, f16),
+        if ((st = check_cuda(launch_check(c, fs, w.v2c, w.c2v, s, w.stats + 1, {}, check_tune, f16,
+                                          it == 1 ? lambda0 : nullptr),
                              "check kernel")))
           break;
         tm.end(s);

@@ -69,6 +69,31 @@ __device__ uint32_t stage_copies(const FrameSet &fs, long long st, int T, long l
   return bytes;
 }
 
+// The first iteration's loads (lambda0 given): V->C of every edge of a variable is still its
+// INITIALIZATION message Lambda0 (Section 3.2), stored once per variable as [frame][variable][z];
+// slot e of check c gets a copy of Lambda0 of its variable. Returns the bytes moved.
+template <typename W>
+__device__ uint32_t stage_copies_l0(const FrameSet &fs, long long st, int T, long long total,
+                                    int M, int k, int N, int Q, const W *l0,
+                                    const int32_t *__restrict__ edge_var, W *sbuf, uint64_t *bar) {
+  const bool narrow = total < (1ll << 32);
+  const uint32_t vb = static_cast<uint32_t>(Q * sizeof(W));
+  uint32_t bytes = 0;
+  const long long end = (st * T + T < total) ? st * T + T : total;
+  for (long long item = st * T; item < end; ++item) {
+    const long long slot = div_m(item, M, narrow);
+    const int c = static_cast<int>(item - slot * M);
+    const int f = frame_id(fs, slot);
+    W *s = sbuf + (size_t)(item - st * T) * k * Q;
+    for (int j = 0; j < k; ++j) {
+      const int v = __ldg(edge_var + (size_t)c * k + j);
+      bulk_load(s + (size_t)j * Q, l0 + ((size_t)f * N + v) * Q, vb, bar);
+      bytes += vb;
+    }
+  }
+  return bytes;
+}
+
 }  // namespace
 
 // Per-warp variant: each warp runs its own S-stage pipeline of tiles of CPW checks (no block
@@ -81,11 +106,12 @@ struct WarpCheck {
   static constexpr int CPW = 32 * EPL / Q;   // checks per warp tile
 };
 
-template <int MB, int KMAX, typename W>
+template <int MB, int KMAX, typename W, bool L0>
 __global__ void __launch_bounds__(256)
     k_check_warp(const W *__restrict__ v2c, W *__restrict__ c2v,
                  const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
-                 int E, int S, FrameSet fs, int32_t *err, LoopTick tick) {
+                 int E, int S, FrameSet fs, int32_t *err, LoopTick tick,
+                 const int32_t *__restrict__ edge_var, int N) {
   using WC = WarpCheck<MB, KMAX>;
   constexpr int Q = WC::Q, EPL = WC::EPL, CPW = WC::CPW;
   griddep_wait();
@@ -119,8 +145,12 @@ __global__ void __launch_bounds__(256)
     const long long first = tj * CPW;
     const long long n = (first + CPW < total ? CPW : total - first);
     mbar_expect_tx(&bars[bj], static_cast<uint32_t>(n * k * Q * sizeof(W)));
-    stage_copies<true, W>(fs, tj, CPW, total, M, k, E, Q, v2c, nullptr,
-                       stages + (size_t)bj * tile_floats, &bars[bj]);
+    if constexpr (L0)
+      stage_copies_l0<W>(fs, tj, CPW, total, M, k, N, Q, v2c, edge_var,
+                         stages + (size_t)bj * tile_floats, &bars[bj]);
+    else
+      stage_copies<true, W>(fs, tj, CPW, total, M, k, E, Q, v2c, nullptr,
+                            stages + (size_t)bj * tile_floats, &bars[bj]);
   };
   if (lane == 0)
     for (; issued < S - 2 && issued < my_count; ++issued) issue(issued);
@@ -166,7 +196,9 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
-                         cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune, bool f16) {
+                         cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune, bool f16,
+                         const float *lambda0) {
+  if (lambda0 && f16) return cudaErrorNotSupported;
   const int Q = c->q, k = c->k;
   const size_t wb = f16 ? 2 : 4;  // bytes per stored message entry
   const int epl = Q < 8 ? Q : 8;
@@ -188,17 +220,21 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
   const long long need = (n_tiles + warps - 1) / warps;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-#define NBFD_CHK_T(MB, KM, W)                                                                \
-  {                                                                                           \
-    const cudaError_t ae = ensure_smem((const void *)k_check_warp<MB, KM, W>, smem);          \
-    if (ae != cudaSuccess) return ae;                                                         \
-    const cudaError_t le = launch_dependent(                                                  \
-        k_check_warp<MB, KM, W>, dim3((int)grid), dim3(warps * 32), smem, s,                  \
-        reinterpret_cast<const W *>(v2c), reinterpret_cast<W *>(c2v), c->d_edge_h, c->d_perm, \
-        c->M, k, c->E, S, fs, err, tick);                                                     \
-    if (le != cudaSuccess) return le;                                                         \
+#define NBFD_CHK_T(MB, KM, W, L0)                                                              \
+  {                                                                                             \
+    const cudaError_t ae = ensure_smem((const void *)k_check_warp<MB, KM, W, L0>, smem);        \
+    if (ae != cudaSuccess) return ae;                                                           \
+    const cudaError_t le = launch_dependent(                                                    \
+        k_check_warp<MB, KM, W, L0>, dim3((int)grid), dim3(warps * 32), smem, s,                \
+        reinterpret_cast<const W *>(L0 ? lambda0 : v2c), reinterpret_cast<W *>(c2v),            \
+        c->d_edge_h, c->d_perm, c->M, k, c->E, S, fs, err, tick, c->d_edge_var, c->N);          \
+    if (le != cudaSuccess) return le;                                                           \
   }
-#define NBFD_CHK(MB, KM) NBFD_CHK_T(MB, KM, float)
+#define NBFD_CHK(MB, KM)                       \
+  {                                            \
+    if (lambda0) NBFD_CHK_T(MB, KM, float, true) \
+    else NBFD_CHK_T(MB, KM, float, false)        \
+  }
 #define NBFD_CHK_M(MB)                     \
   {                                        \
     if (k <= 4) NBFD_CHK(MB, 4)            \
@@ -208,10 +244,10 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
   }
   if (f16) {  // half storage: GF(256) only
     if (c->m != 8) return cudaErrorNotSupported;
-    if (k <= 4) NBFD_CHK_T(8, 4, __half)
-    else if (k <= 8) NBFD_CHK_T(8, 8, __half)
-    else if (k <= 16) NBFD_CHK_T(8, 16, __half)
-    else NBFD_CHK_T(8, 32, __half)
+    if (k <= 4) NBFD_CHK_T(8, 4, __half, false)
+    else if (k <= 8) NBFD_CHK_T(8, 8, __half, false)
+    else if (k <= 16) NBFD_CHK_T(8, 16, __half, false)
+    else NBFD_CHK_T(8, 32, __half, false)
     return cudaGetLastError();
   }
   switch (c->m) {

@@ -95,9 +95,11 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
 inline bool stores_f16(int form) { return (form & NBFD_STORE_F16) != 0; }
 // err (device word, may be NULL) receives NBFD_ETIMEDOUT if a bounded wait of the kernel expired.
 // f16: messages stored as IEEE half (NBFD_STORE_F16); the float pointers then address halves.
+// lambda0 (float storage only): the first iteration's V->C given as Lambda0 once per variable,
+// [frame][variable][z] (the INITIALIZATION's message on both edges); v2c is then unused.
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
                          cudaStream_t s, int32_t *err = nullptr, LoopTick tick = {},
-                         CheckTune tune = {}, bool f16 = false);
+                         CheckTune tune = {}, bool f16 = false, const float *lambda0 = nullptr);
 cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                        const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, cudaStream_t s,
                        int32_t *err = nullptr, VarTune tune = {});
