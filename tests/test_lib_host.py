@@ -101,3 +101,36 @@ def test_python_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(nb, "LIB_PATH", "/nonexistent/libnbfd.so")
     with pytest.raises(ImportError):
         nb.lib()
+
+
+def header_defines():
+    """Integer #define NBFD_* values of include/nbfd.h."""
+    text = open(HEADER).read()
+    out = {}
+    for m in re.finditer(r"#define\s+(NBFD_[A-Z0-9_]+)\s+\(?\s*(-?(?:0x[0-9A-Fa-f]+|\d+))\s*\)?", text):
+        out[m.group(1)] = int(m.group(2), 0)
+    return out
+
+
+def test_binding_constants_equal_the_header():
+    """The Python binding passes forms, flags and kernel ids as plain integers: each must equal
+    the value include/nbfd.h defines."""
+    d = header_defines()
+    pairs = {
+        "NBFD_FORM_FP32_DIRECT": nb.FORM_FP32_DIRECT, "NBFD_FORM_BF16_HGEMM": nb.FORM_BF16_HGEMM,
+        "NBFD_FORM_FP16_HGEMM": nb.FORM_FP16_HGEMM, "NBFD_FORM_FP32_FWHT": nb.FORM_FP32_FWHT,
+        "NBFD_FORM_FP32_TC": nb.FORM_FP32_TC, "NBFD_DECIDE_SYMBOL": nb.DECIDE_SYMBOL,
+        "NBFD_STORE_F16": nb.STORE_F16, "NBFD_BATCH_AUTOTUNE": nb.BATCH_AUTOTUNE,
+        "NBFD_KERNEL_INIT": nb.KERNEL_INIT, "NBFD_KERNEL_CHECK": nb.KERNEL_CHECK,
+        "NBFD_KERNEL_VAR": nb.KERNEL_VAR, "NBFD_KERNEL_SYNDROME": nb.KERNEL_SYNDROME,
+        "NBFD_KERNEL_TAIL": nb.KERNEL_TAIL,
+    }
+    for name, value in pairs.items():
+        assert d[name] == value, name
+    # every kernel id has a timer bit in NBFD_PROF_ALL, and the ids are 0 .. COUNT-1
+    kernels = sorted(v for k, v in d.items() if k.startswith("NBFD_KERNEL_") and k != "NBFD_KERNEL_COUNT")
+    assert kernels == list(range(d["NBFD_KERNEL_COUNT"]))
+    assert d["NBFD_PROF_ALL"] == (1 << d["NBFD_KERNEL_COUNT"]) - 1
+    # status codes are distinct and negative, NBFD_OK is 0
+    errs = [v for k, v in d.items() if k.startswith("NBFD_E")]
+    assert d["NBFD_OK"] == 0 and len(set(errs)) == len(errs) and max(errs) < 0
