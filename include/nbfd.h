@@ -188,9 +188,10 @@ int nbfd_autotune_result(const nbfd_code *code, int n_frames, int form, int *che
                          int *check_stages, int *check_blocks_per_sm, int *var_blocks_per_sm);
 
 /*
- * nbfd_last_decode_stats -- for the calling thread's last successful nbfd_decode: the number of
- * (frame, iteration) pairs where the Fourier-domain syndrome of Section 3.2 cleared while the
- * GF(2^m) syndrome H x_hat was not 0 (the frame went on decoding: the stop test needs both).
+ * nbfd_last_decode_stats -- for the calling thread's last successful nbfd_decode or
+ * nbfd_decode_noalloc: the number of (frame, iteration) pairs where the Fourier-domain syndrome
+ * of Section 3.2 cleared while the GF(2^m) syndrome H x_hat was not 0 (the frame went on
+ * decoding: the stop test needs both).
  * Errors: NBFD_EINVAL (NULL pointer, or no such call in this thread).
  */
 int nbfd_last_decode_stats(long long *fourier_only_clears);
@@ -202,11 +203,14 @@ int nbfd_last_decode_stats(long long *fourier_only_clears);
 #define NBFD_NOALLOC_SCRATCH_BYTES (64ull << 20)
 
 /*
- * nbfd_decode_noalloc -- the same decoding as nbfd_decode (same arguments, same outputs, same
- * once-per-iteration synchronisation with `cuda_stream`), for callers that must not allocate
- * device memory while decoding: a receiver whose device memory another runtime reserved up
- * front, or a real-time loop where cudaMalloc/cudaFree are banned because they may synchronise
- * the device and take unbounded time. It calls no allocating routine.
+ * nbfd_decode_noalloc -- the same decoding as nbfd_decode (the same loop, launch shapes and
+ * synchronisation with `cuda_stream`: the host reads the active-frame count back every few
+ * iterations; the same outputs, status codes -- NBFD_ETIMEDOUT when a bounded device-side wait
+ * expired -- and nbfd_last_decode_stats), for callers that must not allocate device memory while
+ * decoding: a receiver whose device memory another runtime reserved up front, or a real-time loop
+ * where cudaMalloc/cudaFree are banned because they may synchronise the device and take
+ * unbounded time. It calls no allocating routine (host reads go to pageable words on the stack;
+ * nbfd_prof_enable's timers are not used).
  *   - Its scratch is a fixed NBFD_NOALLOC_SCRATCH_BYTES array inside the library, created when the
  *     library's device code is loaded on a device and held on every such device until the
  *     process exits.
@@ -214,7 +218,7 @@ int nbfd_last_decode_stats(long long *fourier_only_clears);
  *     make that first call before any stream capture.
  *   - A batch whose scratch (nbfd_decode_workspace_size) exceeds the array is rejected with
  *     NBFD_ENOMEM and a message; split it into smaller calls. At GF(256), N = 512 and
- *     max_iter <= 100 that is up to 31 frames per call.
+ *     max_iter <= 100 that is up to 31 frames per call (62 with NBFD_STORE_F16).
  *   - Every call uses the same array and clears what it needs at its start. Calls whose GPU work
  *     can overlap (different streams without ordering between them, or several host threads)
  *     race on the array and corrupt each other's results: order them.
@@ -360,7 +364,6 @@ int nbfd_prof_enable(int kernel_mask);
  * launches of the number of frames the launch processed). Any out pointer may be NULL. */
 int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_units);
 
-/* Message for the calling thread's last failed call ("" if none). */
 /* ---- diagnostics (no counterpart in the paper) ----------------------------------------------
  * nbfd_diag_wait_expiry -- run the expiry path of the bounded device-side waits on purpose: one
  * thread waits, with the kernels' bounded mbarrier wait and a budget of budget_cycles SM cycles
@@ -369,6 +372,16 @@ int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_
  * one of its waits expires) and the CUDA context stays usable. Synchronises `cuda_stream`. */
 int nbfd_diag_wait_expiry(long long budget_cycles, void *cuda_stream);
 
+/*
+ * nbfd_diag_preset_status -- the next nbfd_decode or nbfd_decode_noalloc of the calling thread
+ * starts its device status word (where a kernel whose bounded wait expired writes
+ * NBFD_ETIMEDOUT) at `value` instead of 0; one-shot. The kernels only ever write that word, so the
+ * decode runs as usual and a nonzero value must come back as NBFD_ETIMEDOUT: it shows on the host,
+ * with no device fault, that an entry point reads its status word back. 0 cancels a preset.
+ */
+int nbfd_diag_preset_status(int32_t value);
+
+/* Message for the calling thread's last failed call ("" if none). */
 const char *nbfd_last_error(void);
 /* Static name of a status code. */
 const char *nbfd_status_string(int status);

@@ -20,6 +20,7 @@ __all__ = [
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
     "STORE_F16", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
+    "nbfd_diag_preset_status",
     "nbfd_last_decode_stats",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
@@ -58,6 +59,7 @@ SIGNATURES = [
     ("nbfd_autotune", _I, [_P, _I, _I, _P]),
     ("nbfd_init_messages_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_diag_wait_expiry", _I, [ctypes.c_longlong, _P]),
+    ("nbfd_diag_preset_status", _I, [ctypes.c_int32]),
     ("nbfd_last_decode_stats", _I, [_P]),
     ("nbfd_check_update_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P]),
@@ -208,6 +210,12 @@ def nbfd_last_decode_stats():
 def nbfd_diag_wait_expiry(budget_cycles, stream=None):
     """Runs the bounded-wait expiry path on purpose; raises NbfdError(NBFD_ETIMEDOUT)."""
     _check(lib().nbfd_diag_wait_expiry(int(budget_cycles), _stream(stream)))
+
+
+def nbfd_diag_preset_status(value):
+    """The calling thread's next nbfd_decode / nbfd_decode_noalloc starts its device status word
+    at `value` (one-shot); a nonzero value must come back as NbfdError(NBFD_ETIMEDOUT)."""
+    _check(lib().nbfd_diag_preset_status(int(value)))
 
 
 def nbfd_init_messages_f16(handle, n_frames, llr, v2c, stream=None):

@@ -95,20 +95,24 @@ class Timers {
   std::vector<PendingTimer> pending_;
 };
 
-// ---- workspace layout ----------------------------------------------------------------------
-struct Workspace {
-  float *v2c, *c2v;
-  uint8_t *fsyn;
-  int32_t *list[2];
-  int32_t *count;  // [max_iter + 2]
-  int32_t *stats;  // [16]
-  size_t bytes;
-};
+int check_device(const nbfd_code *c) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != c->device)
+    return set_error(NBFD_EINVAL, "current device %d differs from the code's device %d", dev,
+                     c->device);
+  return NBFD_OK;
+}
 
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
 
-Workspace carve(const nbfd_code *c, int F, int max_iter, int form, char *base) {
-  Workspace w{};
+// ---- workspace layout (shared by nbfd_decode and nbfd_decode_noalloc) -----------------------
+namespace nbfd {
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+DecodeScratch carve_decode_scratch(const nbfd_code *c, int F, int max_iter, int form, char *base) {
+  DecodeScratch w{};
   const size_t msg = align256((size_t)F * c->E * c->q * (stores_f16(form) ? 2 : 4));
   size_t off = 0;
   w.v2c = reinterpret_cast<float *>(base + off);
@@ -129,16 +133,7 @@ Workspace carve(const nbfd_code *c, int F, int max_iter, int form, char *base) {
   return w;
 }
 
-int check_device(const nbfd_code *c) {
-  int dev = -1;
-  cudaGetDevice(&dev);
-  if (dev != c->device)
-    return set_error(NBFD_EINVAL, "current device %d differs from the code's device %d", dev,
-                     c->device);
-  return NBFD_OK;
-}
-
-}  // namespace
+}  // namespace nbfd
 
 extern "C" int nbfd_prof_enable(int kernel_mask) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -159,11 +154,12 @@ extern "C" int nbfd_prof_get(int kernel, double *ms, long long *launches, long l
 extern "C" size_t nbfd_decode_workspace_size(const nbfd_code *c, int n_frames, int max_iter,
                                              int form) {
   if (!c || n_frames < 0 || max_iter < 0) return 0;
-  return carve(c, n_frames, max_iter, form, nullptr).bytes;
+  return carve_decode_scratch(c, n_frames, max_iter, form, nullptr).bytes;
 }
 
-// the disagreement count of the calling thread's last nbfd_decode (nbfd_last_decode_stats)
-thread_local long long g_last_fourier_only = -1;
+// the disagreement count of the calling thread's last nbfd_decode or nbfd_decode_noalloc
+// (nbfd_last_decode_stats)
+static thread_local long long g_last_fourier_only = -1;
 
 // A pinned host word per host thread for the active-frame count, allocated on first use and kept
 // for the thread's lifetime (a per-call cudaMallocHost / cudaFreeHost pair would synchronise the
@@ -191,34 +187,26 @@ extern "C" int nbfd_last_decode_stats(long long *fourier_only_clears) {
   return NBFD_OK;
 }
 
-extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
-                           uint16_t *symbols, uint8_t *ok, int32_t *iters, void *workspace,
-                           size_t workspace_bytes, void *stream_) {
-  if (!c) return set_error(NBFD_EINVAL, "code is NULL");
-  if (F < 0) return set_error(NBFD_EINVAL, "n_frames < 0");
-  if (max_iter < 1) return set_error(NBFD_EINVAL, "max_iter must be >= 1");
-  if (!form_supported(form, c->m)) return set_error(NBFD_ENOTSUP, "form %d not supported", form);
-  if (F == 0) return NBFD_OK;
-  if (!llr || !symbols || !ok || !iters) return set_error(NBFD_EINVAL, "NULL buffer");
-  if (int st = check_device(c)) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream_);
-  const size_t need = nbfd_decode_workspace_size(c, F, max_iter, form);
-  bool owned = false;
-  if (workspace == nullptr) {
-    if (int st = check_cuda(cudaMallocAsync(&workspace, need, s), "cudaMallocAsync(workspace)"))
-      return st;
-    owned = true;
-  } else if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
-    return set_error(NBFD_ENOMEM, "workspace of %zu bytes (need %zu, 256-byte aligned)",
-                     workspace_bytes, need);
-  }
-  Workspace w = carve(c, F, max_iter, form, static_cast<char *>(workspace));
+namespace {
+// nbfd_diag_preset_status: the value the next decode of this thread starts its status word with
+thread_local int32_t g_preset_status = 0;
+}  // namespace
+
+extern "C" int nbfd_diag_preset_status(int32_t value) {
+  g_preset_status = value;
+  return NBFD_OK;
+}
+
+namespace nbfd {
+
+int decode_loop(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
+                uint16_t *symbols, uint8_t *ok, int32_t *iters, const DecodeScratch &w,
+                int32_t *host_words, bool timers, cudaStream_t s) {
   const bool f16 = stores_f16(form);
-  int32_t *host_count = nullptr;
   int st = NBFD_OK;
   g_last_fourier_only = -1;
-  int prof_mask;
-  {
+  int prof_mask = 0;
+  if (timers) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof_mask = g_prof_mask;
   }
@@ -226,15 +214,24 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
   CheckTune check_tune;
   VarTune var_tune;
   tune_lookup(c, F, form, &check_tune, &var_tune);  // shapes from nbfd_autotune, if any
+  const int32_t preset = g_preset_status;
+  g_preset_status = 0;
   do {
-    if (!(host_count = pinned_word())) {
-      st = set_error(NBFD_ECUDA, "cudaHostAlloc of the count word failed");
-      break;
-    }
-    if ((st = check_cuda(cudaMemsetAsync(w.count, 0, (size_t)(max_iter + 2) * 4 + 0, s),
+    // the scratch may hold anything (a caller's workspace, or the previous no-allocation call's
+    // leftovers): clear every counter and status word the loop relies on
+    if ((st = check_cuda(cudaMemsetAsync(w.count, 0, (size_t)(max_iter + 2) * 4, s),
                          "cudaMemsetAsync")))
       break;
     if ((st = check_cuda(cudaMemsetAsync(w.stats, 0, 64, s), "cudaMemsetAsync"))) break;
+    if (preset != 0) {
+      host_words[0] = preset;
+      if ((st = check_cuda(cudaMemcpyAsync(w.stats + 1, host_words, sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s),
+                           "cudaMemcpyAsync(preset status)")))
+        break;
+      // the copy reads host_words before host_words is written again below
+      if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
+    }
     if ((st = check_cuda(cudaMemsetAsync(ok, 0, (size_t)F, s), "cudaMemsetAsync"))) break;
     // Once the frames left fit the tail kernel's resident clusters, one launch runs all their
     // remaining iterations (one thread-block cluster per frame).
@@ -306,25 +303,25 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
         tm.end(s);
       }
       if (st) break;
-      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.count + it, sizeof(int32_t),
+      if ((st = check_cuda(cudaMemcpyAsync(host_words, w.count + it, sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s),
                            "cudaMemcpyAsync(count)")))
         break;
       if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
-      active = *host_count;
+      active = host_words[0];
     }
     if (st == NBFD_OK) {
       // stats[0] counts iterations where a frame's Fourier-domain syndrome cleared while its
       // GF(2^m) syndrome did not; stats[1] holds NBFD_ETIMEDOUT if a bounded wait expired
-      if ((st = check_cuda(cudaMemcpyAsync(host_count, w.stats, 2 * sizeof(int32_t),
+      if ((st = check_cuda(cudaMemcpyAsync(host_words, w.stats, 2 * sizeof(int32_t),
                                            cudaMemcpyDeviceToHost, s),
                            "cudaMemcpyAsync(status)")))
         break;
       if ((st = check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) break;
-      g_last_fourier_only = host_count[0];
-      if (host_count[1] != 0)
+      g_last_fourier_only = host_words[0];
+      if (host_words[1] != 0)
         st = set_error(NBFD_ETIMEDOUT, "a bounded device-side wait expired (status %d)",
-                       host_count[1]);
+                       host_words[1]);
     }
     if (st == NBFD_OK && tm.on()) {
       std::vector<int32_t> counts((size_t)max_iter + 2, 0);
@@ -335,6 +332,36 @@ extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_
       tm.flush(counts, F);
     }
   } while (false);
+  return st;
+}
+
+}  // namespace nbfd
+
+extern "C" int nbfd_decode(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
+                           uint16_t *symbols, uint8_t *ok, int32_t *iters, void *workspace,
+                           size_t workspace_bytes, void *stream_) {
+  if (!c) return set_error(NBFD_EINVAL, "code is NULL");
+  if (F < 0) return set_error(NBFD_EINVAL, "n_frames < 0");
+  if (max_iter < 1) return set_error(NBFD_EINVAL, "max_iter must be >= 1");
+  if (!form_supported(form, c->m)) return set_error(NBFD_ENOTSUP, "form %d not supported", form);
+  if (F == 0) return NBFD_OK;
+  if (!llr || !symbols || !ok || !iters) return set_error(NBFD_EINVAL, "NULL buffer");
+  if (int st = check_device(c)) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream_);
+  const size_t need = nbfd_decode_workspace_size(c, F, max_iter, form);
+  int32_t *host_words = pinned_word();
+  if (!host_words) return set_error(NBFD_ECUDA, "cudaHostAlloc of the count word failed");
+  bool owned = false;
+  if (workspace == nullptr) {
+    if (int st = check_cuda(cudaMallocAsync(&workspace, need, s), "cudaMallocAsync(workspace)"))
+      return st;
+    owned = true;
+  } else if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+    return set_error(NBFD_ENOMEM, "workspace of %zu bytes (need %zu, 256-byte aligned)",
+                     workspace_bytes, need);
+  }
+  const DecodeScratch w = carve_decode_scratch(c, F, max_iter, form, static_cast<char *>(workspace));
+  const int st = decode_loop(c, F, llr, max_iter, form, symbols, ok, iters, w, host_words, true, s);
   if (owned) cudaFreeAsync(workspace, s);
   return st;
 }

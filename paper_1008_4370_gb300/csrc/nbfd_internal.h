@@ -66,6 +66,25 @@ inline int oversubscribed_waves(long long work, long long warps_per_wave) {
 // Launch shapes cached by the autotuner for (device, code shape, n_frames, form), if any.
 bool tune_lookup(const nbfd_code *c, int F, int form, CheckTune *ct, VarTune *vt);
 
+// Scratch of one decoding loop, carved from one 256-byte aligned block (nbfd_decode's workspace
+// or nbfd_decode_noalloc's fixed array); bytes is the block size it needs (base may be NULL).
+struct DecodeScratch {
+  float *v2c, *c2v;  // messages [F][E][q], float or (NBFD_STORE_F16) half words
+  uint8_t *fsyn;     // [F][E] per-edge Fourier syndrome words
+  int32_t *list[2];  // active-frame lists, ping-pong
+  int32_t *count;    // [max_iter + 2] active count per iteration
+  int32_t *stats;    // [16]: [0] Fourier-only clears, [1] NBFD_ETIMEDOUT if a bounded wait expired
+  size_t bytes;
+};
+DecodeScratch carve_decode_scratch(const nbfd_code *c, int F, int max_iter, int form, char *base);
+// The decoding loop of nbfd_decode on the scratch w (arguments already validated). host_words:
+// two int32 host words for the count and status read-backs (pinned or pageable). timers: honour
+// nbfd_prof_enable. Sets the calling thread's nbfd_last_decode_stats; returns NBFD_ETIMEDOUT if
+// a kernel's bounded wait expired.
+int decode_loop(const nbfd_code *c, int F, const float *llr, int max_iter, int form,
+                uint16_t *symbols, uint8_t *ok, int32_t *iters, const DecodeScratch &w,
+                int32_t *host_words, bool timers, cudaStream_t s);
+
 int set_error(int status, const char *fmt, ...);
 int check_cuda(cudaError_t e, const char *what);
 int sm_count();
