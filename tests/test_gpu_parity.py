@@ -16,7 +16,8 @@ from oracle.code import OracleCode  # noqa: E402
 from paper_1008_4370_gb300 import build as nbuild  # noqa: E402
 from paper_1008_4370_gb300 import synth  # noqa: E402
 
-from helpers import MARGIN, compare, decode_pair, encode, oracle_state, var_conditions, vn_margins  # noqa: E402
+from helpers import (MARGIN, compare, decode_pair, encode, log_exempt_cap, oracle_decodes, oracle_state,  # noqa: E402
+                     var_conditions, var_log_conditions, vn_margins)
 
 pytestmark = pytest.mark.gpu
 
@@ -172,7 +173,11 @@ def test_var_parity(dev, spec, form):
         kappa = var_conditions(oc, lam0, c2v_o)
         floor, kf, logb, margin = _tolerances(form)
         if floor is None:
-            ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es])
+            ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es],
+                             kappa_log=var_log_conditions(oc, lam0, c2v_o)[es])
+            # frame 1 carries saturated +-45 LLRs against its check messages on purpose (U(0) tiny):
+            # its share of entries left out of the log check is not capped
+            assert f == 1 or st["exempt"] <= log_exempt_cap(oc.m), (f, st)
         else:
             ok, st = compare(g[f][es], s[es], l[es], kappa=kappa[es] * kf / 2.0 ** -24, lin_atol=floor,
                              log_atol=logb)
@@ -212,6 +217,9 @@ def test_syndrome_parity(dev):
     assert not ex.cpu().numpy()[0].any()
 
 
+_ORACLE_CACHE = {}
+
+
 def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5, form=nb.FORM_FP32_DIRECT,
                       decision="bitwise"):
     """Whole decodes on both sides. Bit-exact symbols and syndrome flags are required on frames
@@ -225,8 +233,13 @@ def _decode_vs_oracle(dev, c, llr, max_iter, frames=None, min_frac=0.5, form=nb.
     torch.cuda.synchronize()
     sym, ok, it = sym.cpu().numpy().astype(np.int64), ok.cpu().numpy(), it.cpu().numpy()
     n_sym = n_it = 0
-    for f in (range(F) if frames is None else frames):
-        r = LF.decode(oc, llr[f].astype(np.float64), max_iter, decision=decision)
+    fl = list(range(F) if frames is None else frames)
+    key = (c.get("name"), max_iter, decision, tuple(fl), hash(llr[fl].tobytes()))
+    if key not in _ORACLE_CACHE:  # the same frames are decoded with several forms
+        _ORACLE_CACHE[key] = oracle_decodes(c, llr[fl], max_iter, decision) if len(fl) > 8 else \
+            [LF.decode(oc, llr[f].astype(np.float64), max_iter, decision=decision) for f in fl]
+    res = _ORACLE_CACHE[key]
+    for f, r in zip(fl, res):
         if r["margins"][-1] > MARGIN and (r["ok"] or r["iters"] == max_iter and max_iter <= 4):
             n_sym += 1
             assert np.array_equal(sym[f], r["symbols"]), f
@@ -313,14 +326,21 @@ def test_decode_edge_cases(dev):
     assert ei.value.status == -10
 
 
+# 16 frames spread over a batch, first and last included
+SPREAD_1024 = [int(x) for x in np.linspace(0, 1023, 16)]
+SPREAD_4096 = [int(x) for x in np.linspace(0, 4095, 16)]
+
+
 @pytest.mark.parametrize("form", FORMS + [nb.FORM_FP32_TC])
 def test_decode_full_size_gf256_n512(dev, form):
     """The measured configuration: GF(256) (2,4) N=512, 1024 frames at Eb/N0 = 1.5 dB. With at
-    most 4 iterations two sampled frames are decoded by the oracle as well; with 100 iterations
-    every frame is checked for properties that hold at any size."""
+    most 10 iterations 16 frames spread over the batch (so over the grid's waves and the
+    bulk-copy pipelines' stages) are decoded by the oracle as well, and compared wherever they
+    converged with a clear margin; with 100 iterations every frame is checked for properties
+    that hold at any size."""
     c = synth.named_code("gf256_n512_k4")
     tx, llr = synth.frames(c, 1024, 1.5)
-    _decode_vs_oracle(dev, c, llr, 4, frames=[0, 777], min_frac=0.5, form=form)
+    _decode_vs_oracle(dev, c, llr, 10, frames=SPREAD_1024, min_frac=0.6, form=form)
     code = nb.Code(c)
     sym, ok, it = nb.decode(code, _t(llr, dev), 100, form)
     # self-consistency on every frame: the library's own syndrome of its output is 0 iff ok
@@ -341,13 +361,13 @@ def test_decode_full_size_gf256_n512(dev, form):
 @pytest.mark.parametrize("form", FORMS)
 def test_decode_full_size_gf64_n1200(dev, form):
     """The plain batched configuration: GF(64) (2,6) N=1200, 4096 frames per launch, Eb/N0 over
-    1.0 .. 3.0 dB (here 2.5 dB, where most frames decode), random codewords. Two sampled frames
-    are decoded by the oracle too (4 iterations); with 100 iterations every frame is checked for
-    what holds at any size."""
+    1.0 .. 3.0 dB (here 2.5 dB, where most frames decode), random codewords. 16 frames spread
+    over the batch are decoded by the oracle too (at most 10 iterations); with 100 iterations
+    every frame is checked for what holds at any size."""
     c = synth.named_code("gf64_n1200_k6")
     enc = synth.Encoder(c)
     tx, llr = synth.frames(c, 4096, 2.5, snr_idx=3, encoder=enc)
-    _decode_vs_oracle(dev, c, llr, 4, frames=[7, 4095], min_frac=1.0, form=form)
+    _decode_vs_oracle(dev, c, llr, 10, frames=SPREAD_4096, min_frac=0.6, form=form)
     code = nb.Code(c)
     sym, ok, it = nb.decode(code, _t(llr, dev), 100, form)
     ex = torch.empty((4096, code.M), dtype=torch.int16, device=dev)

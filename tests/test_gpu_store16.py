@@ -16,7 +16,8 @@ from oracle.code import OracleCode  # noqa: E402
 from paper_1008_4370_gb300 import build as nbuild  # noqa: E402
 from paper_1008_4370_gb300 import synth  # noqa: E402
 
-from helpers import compare_store16, decode_pair, encode, oracle_state, to_half, var_conditions  # noqa: E402
+from helpers import (compare_store16, decode_pair, encode, log_exempt_cap, oracle_state, to_half,  # noqa: E402
+                     var_conditions, var_log_conditions)
 
 pytestmark = pytest.mark.gpu
 
@@ -127,7 +128,9 @@ def test_var_store16(dev, spec):
         vs = np.arange(oc.N) if vars_ is None else np.array(vars_)
         es = np.concatenate([oc.C[v] for v in vs])
         kappa = var_conditions(oc, lam0, c2v_o)
-        ok, st = compare_store16(g[f][es], s[es], l[es], kappa=kappa[es])
+        ok, st = compare_store16(g[f][es], s[es], l[es], kappa=kappa[es],
+                                 kappa_log=var_log_conditions(oc, lam0, c2v_o)[es])
+        assert f == 1 or st["exempt"] <= log_exempt_cap(oc.m), (f, st)  # frame 1: saturated LLRs
         assert ok, (f, st)
 
 
