@@ -34,7 +34,6 @@ if ROOT not in sys.path:
 from paper_1008_4370_gb300 import synth  # noqa: E402
 
 CODE_NAME = "gf256_n512_k4"
-FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 
 # DRAM bytes per frame of one launch, from one ncu capture of a 256-frame launch with every frame
@@ -85,6 +84,8 @@ def parse():
                     help="steps of the half-precision message storage leg (0: skip)")
     ap.add_argument("--uneven-steps", type=int, default=3,
                     help="steps of the uneven five-code batch leg (0: skip)")
+    ap.add_argument("--gf64-steps", type=int, default=2,
+                    help="timed steps per point of the GF(64) N=1200 plain batched sweep (0: skip)")
     ap.add_argument("--prof-steps", type=int, default=8,
                     help="leading steps of the timed region with per-launch kernel timers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -249,6 +250,80 @@ def reference_mean_iterations():
         with open(p) as f:
             return float(json.load(f)["mean_iterations"])
     return None
+
+
+def clopper_pearson(k: int, n: int, alpha: float = 0.05):
+    """Exact 95% interval of a frame error rate (None without scipy)."""
+    try:
+        from scipy.stats import beta
+    except ImportError:
+        return None
+    lo = 0.0 if k == 0 else float(beta.ppf(alpha / 2, k, n - k + 1))
+    hi = 1.0 if k == n else float(beta.ppf(1 - alpha / 2, k + 1, n - k))
+    return [lo, hi]
+
+
+def fp32_peak(nb):
+    """Measured FP32 FMA rate (TFLOP/s) with scalar and packed (f32x2) FMA chains."""
+    out = {}
+    for name, packed in (("scalar", 0), ("packed_f32x2", 1)):
+        t, ms = nb.nbfd_diag_fp32_rate(packed, 4, 1 << 20)
+        out[name] = {"tflops": t, "ms": ms}
+    out["peak_tflops"] = max(v["tflops"] for v in out.values())
+    return out
+
+
+GF64_POINTS = (1.0, 1.5, 2.0, 2.5, 3.0)
+
+
+def gf64_leg(nb, torch, dev, steps, max_iter, peak_gbs, F=4096):
+    """The plain batched configuration: GF(64) (2,6) N=1200, 4096 frames per launch, random
+    codewords, Eb/N0 over 1.0 .. 3.0 dB, max_iter iterations with early stop. Per point and form:
+    decoded Mbit/s (device time, CUDA events), FER with its 95% Clopper-Pearson interval, mean
+    iterations, and the HBM fraction of the iteration kernels (check + variable node, algorithmic
+    bytes / their launch time)."""
+    c = synth.named_code("gf64_n1200_k6")
+    enc = synth.Encoder(c)
+    code = nb.Code(c)
+    m, N, E, q = c["m"], c["N"], 2 * c["N"], 1 << c["m"]
+    bits = enc.info_symbols * m
+    stream = torch.cuda.current_stream()
+    sym = torch.empty((F, N), dtype=torch.int16, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    its = torch.empty(F, dtype=torch.int32, device=dev)
+    need = max(nb.nbfd_decode_workspace_size(code.handle, F, max_iter, f) for f in (FORMS["fwht"], FORMS["direct"]))
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    rows = []
+    for si, ebn0 in enumerate(GF64_POINTS):
+        tx, llr = synth.frames(c, F, ebn0, snr_idx=si, batch_idx=500, encoder=enc)
+        x = torch.from_numpy(llr).to(dev)
+        for fname in ("fwht", "direct"):
+            form = FORMS[fname]
+
+            def dec():
+                nb.nbfd_decode(code.handle, F, x, max_iter, form, sym, ok, its, ws, need, stream)
+
+            nb.nbfd_prof_enable((1 << nb.KERNEL_CHECK) | (1 << nb.KERNEL_VAR))
+            dec()
+            torch.cuda.synchronize()
+            (cms, _, cu), (vms, _, vu) = nb.nbfd_prof_get(nb.KERNEL_CHECK), nb.nbfd_prof_get(nb.KERNEL_VAR)
+            nb.nbfd_prof_enable(0)
+            wrong = int((~np.all(sym.cpu().numpy().astype(np.int64) == tx, axis=1)).sum())
+            mean_it = float(its.float().mean())
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for i in range(steps):
+                ev[i][0].record(stream)
+                dec()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / steps
+            it_bytes = cu * 2 * E * q * 4 + vu * (2 * E * q * 4 + N * m * 4 + N * 2 + E)
+            rows.append({"ebn0_db": ebn0, "form": fname, "mbit_s": bits * F / (ms / 1e3) / 1e6, "ms_per_step": ms,
+                         "fer": wrong / F, "fer_ci95": clopper_pearson(wrong, F), "mean_iterations": mean_it,
+                         "iteration_kernels_hbm_frac": it_bytes / ((cms + vms) / 1e3) / 1e9 / peak_gbs,
+                         "check_ms": cms, "var_ms": vms})
+    return {"code": "gf64_n1200_k6", "frames": F, "max_iter": max_iter, "steps_per_point": steps,
+            "info_bits_per_frame": bits, "points": rows}
 
 
 UNEVEN = [("gf16_n96_k4", 8192), ("gf64_n1200_k6", 2048), ("gf64_n4096_k8", 512),
@@ -536,8 +611,21 @@ def run_ours(a):
         torch.cuda.synchronize()
         p_s = sum(x.elapsed_time(y) for x, y in pe) / 1e3
         p_t, p_value = aggregate(p_s, F * a.plain_steps, info_bits, dist if world > 1 else None, dev)
+        # FER of the plain form on every batch, and its variable-node launches timed (one decode)
+        p_fail = 0
+        for b in range(len(batches)):
+            nb.nbfd_decode(code.handle, F, batches[b][1], a.max_iter, FORMS["direct"], sym, ok, its, ws, need,
+                           stream)
+            torch.cuda.synchronize()
+            p_fail += int((ok == 0).sum().item())
+        nb.nbfd_prof_enable(1 << nb.KERNEL_VAR)
+        nb.nbfd_decode(code.handle, F, batches[0][1], a.max_iter, FORMS["direct"], sym, ok, its, ws, need, stream)
+        torch.cuda.synchronize()
+        pv_ms, pv_launches, pv_units = nb.nbfd_prof_get(nb.KERNEL_VAR)
+        nb.nbfd_prof_enable(0)
         plain = {"form": "direct", "value": p_value, "unit": "Mbit/s", "steps": a.plain_steps,
-                 "ms_per_step": 1e3 * p_t / a.plain_steps}
+                 "ms_per_step": 1e3 * p_t / a.plain_steps, "fer": p_fail / (F * len(batches)),
+                 "var_kernel": {"ms": pv_ms, "launches": pv_launches, "frame_units": pv_units}}
     # serving leg: continuous batching of single-frame requests of this code
     # the same workload with half-precision message storage (FP32 arithmetic): a lower-precision
     # form of its own, reported beside the FP32 headline
@@ -572,13 +660,18 @@ def run_ours(a):
         llr_all = np.concatenate(pool, axis=0)
         reps = (R + llr_all.shape[0] - 1) // llr_all.shape[0]
         llr_req = np.concatenate([llr_all] * reps, axis=0)[:R]
-        got, wall, ph = serve_run(nb, [(code, llr_req, None, a.max_iter, info_bits)], form, 32 << 30)
-        sat = serve_summary(got, wall, ph)
+        got, swall, ph = serve_run(nb, [(code, llr_req, None, a.max_iter, info_bits)], form, 32 << 30)
+        sat = serve_summary(got, swall, ph)
         rng = synth.rng_for(23, R)
         arr = np.cumsum(rng.exponential(1.0 / a.serve_load, size=R))
         got2, wall2, ph2 = serve_run(nb, [(code, llr_req, arr, a.max_iter, info_bits)], form, 32 << 30)
         ld = serve_summary(got2, wall2, ph2, a.serve_load)
         served = {"form": a.form, "saturation": sat, "poisson": ld}
+    peaks, peak_kind = load_peaks()
+    gf64 = None
+    if a.gf64_steps > 0 and world == 1:
+        gf64 = gf64_leg(nb, torch, dev, a.gf64_steps, a.max_iter, float(peaks["hbm_gbs"]))
+    fp32 = fp32_peak(nb) if rank == 0 else None
     # the uneven five-code batch last: it holds about 9 GB while it runs
     uneven = None
     if a.uneven_steps > 0 and world == 1 and (form & 0xff) in (FORMS["fwht"], FORMS["direct"]):
@@ -590,18 +683,17 @@ def run_ours(a):
         return
 
     # roofline of the dominant kernel
-    peaks, peak_kind = load_peaks()
     names = {0: "init", 1: "check", 2: "var", 3: "syndrome"}
     dom = max(prof, key=lambda k: prof[k][0])
     ms, launches, units = prof[dom]
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    flops_per_frame = 2.0 * (E * q * q + 3 * m * q * N)  # the direct form's q^2 FMAs per edge
     if dom == 2 and form == 0:
-        flops_per_frame = 2.0 * (E * q * q + 3 * m * q * N)
         achieved = flops_per_frame * units / (ms / 1e3) / 1e12
-        peak = sm_count * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        peak = fp32["peak_tflops"]
         roof = {"bound": "alu", "kernel": "k_var_direct", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x max SM clock"}
+                "peak_source": "measured FP32 FMA rate (nbfd_diag_fp32_rate)"}
     else:
         bytes_per_frame = {
             0: N * m * 4 + E * q * 4,
@@ -638,6 +730,12 @@ def run_ours(a):
                          f"{fi} frame-iterations in {wall_c:.1f} s, converted at {it_ref:.2f} "
                          f"iterations per frame ({it_src})"}
 
+    if plain is not None and plain["var_kernel"]["ms"] > 0:
+        pv = plain["var_kernel"]
+        achieved = flops_per_frame * pv["frame_units"] / (pv["ms"] / 1e3) / 1e12
+        plain["roofline"] = {"bound": "alu", "kernel": "k_var_direct", "achieved": achieved,
+                             "peak": fp32["peak_tflops"], "unit": "TFLOP/s", "frac": achieved / fp32["peak_tflops"],
+                             "peak_source": "measured FP32 FMA rate (nbfd_diag_fp32_rate)"}
     line = {
         "metric": "decoded Mbit/s (GF(256) (2,4) N=512)", "value": value, "unit": "Mbit/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps,
@@ -656,6 +754,8 @@ def run_ours(a):
         "plain_fp32": plain,
         "store16": store16,
         "uneven_batch": uneven,
+        "plain_batch_gf64": gf64,
+        "fp32_peak": fp32,
         "served": served,
         "gpu_launches": launches_total,
         "roofline": roof,

@@ -373,6 +373,17 @@ int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_
 int nbfd_diag_wait_expiry(long long budget_cycles, void *cuda_stream);
 
 /*
+ * nbfd_diag_fp32_rate -- measured FP32 FMA rate of the device (no tensor cores), the peak the FP32
+ * forms of the variable node are compared against: sm_count * blocks_per_sm blocks of 256
+ * threads, each thread running 8 independent chains of `iters` FMAs (packed = 0: scalar fma.f32;
+ * packed = 1: fma.f32x2, two lanes per instruction). One warm-up launch, then one launch timed
+ * with CUDA events on `cuda_stream`. *tflops = 2 * FMAs / time (1e12 flop/s); *ms (may be NULL)
+ * = the timed launch. blocks_per_sm in [1, 8], iters in [1, 2^30]. Synchronises `cuda_stream`.
+ */
+int nbfd_diag_fp32_rate(int packed, int blocks_per_sm, long long iters, double *tflops, double *ms,
+                        void *cuda_stream);
+
+/*
  * nbfd_diag_preset_status -- the next nbfd_decode or nbfd_decode_noalloc of the calling thread
  * starts its device status word (where a kernel whose bounded wait expired writes
  * NBFD_ETIMEDOUT) at `value` instead of 0; one-shot. The kernels only ever write that word, so the

@@ -20,7 +20,7 @@ __all__ = [
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
     "STORE_F16", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
-    "nbfd_diag_preset_status",
+    "nbfd_diag_preset_status", "nbfd_diag_fp32_rate",
     "nbfd_last_decode_stats",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
@@ -60,6 +60,7 @@ SIGNATURES = [
     ("nbfd_init_messages_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_diag_wait_expiry", _I, [ctypes.c_longlong, _P]),
     ("nbfd_diag_preset_status", _I, [ctypes.c_int32]),
+    ("nbfd_diag_fp32_rate", _I, [_I, _I, ctypes.c_longlong, _P, _P, _P]),
     ("nbfd_last_decode_stats", _I, [_P]),
     ("nbfd_check_update_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P]),
@@ -210,6 +211,14 @@ def nbfd_last_decode_stats():
 def nbfd_diag_wait_expiry(budget_cycles, stream=None):
     """Runs the bounded-wait expiry path on purpose; raises NbfdError(NBFD_ETIMEDOUT)."""
     _check(lib().nbfd_diag_wait_expiry(int(budget_cycles), _stream(stream)))
+
+
+def nbfd_diag_fp32_rate(packed=0, blocks_per_sm=4, iters=1 << 20, stream=None):
+    """Measured FP32 FMA rate: (TFLOP/s, ms of the timed launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().nbfd_diag_fp32_rate(int(packed), int(blocks_per_sm), int(iters), ctypes.byref(t),
+                                     ctypes.byref(ms), _stream(stream)))
+    return t.value, ms.value
 
 
 def nbfd_diag_preset_status(value):

@@ -47,3 +47,82 @@ extern "C" int nbfd_diag_wait_expiry(long long budget_cycles, void *stream_) {
   if (h == NBFD_ETIMEDOUT) return set_error(NBFD_ETIMEDOUT, "bounded wait expired (as arranged)");
   return h;
 }
+
+// ---- FP32 FMA rate ---------------------------------------------------------------------------
+// Peak of the FP32 pipe (no tensor cores): every thread runs 8 independent FMA chains
+// a = a * x + y (x slightly below 1, so the values converge and never overflow or go subnormal),
+// scalar fmaf or packed __ffma2_rn (two lanes per instruction). The chains' sum is stored only if
+// it equals a value it cannot reach, which keeps them live without a store per thread.
+namespace {
+
+constexpr int kFmaThreads = 256;
+constexpr int kFmaChains = 8;
+
+template <bool kPacked>
+__global__ void __launch_bounds__(kFmaThreads) k_fma_rate(long long iters, float x, float y,
+                                                          float *sink) {
+  float s = 0.0f;
+  if constexpr (kPacked) {
+    float2 a[kFmaChains];
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i)
+      a[i] = make_float2(1e-3f * (threadIdx.x & 7) + i, 0.5f * i);
+    const float2 xx = make_float2(x, x), yy = make_float2(y, y);
+    for (long long n = 0; n < iters; ++n) {
+#pragma unroll
+      for (int i = 0; i < kFmaChains; ++i) a[i] = __ffma2_rn(a[i], xx, yy);
+    }
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i) s += a[i].x + a[i].y;
+  } else {
+    float a[kFmaChains];
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i) a[i] = 1e-3f * (threadIdx.x & 7) + i;
+    for (long long n = 0; n < iters; ++n) {
+#pragma unroll
+      for (int i = 0; i < kFmaChains; ++i) a[i] = fmaf(a[i], x, y);
+    }
+#pragma unroll
+    for (int i = 0; i < kFmaChains; ++i) s += a[i];
+  }
+  if (s == -1.0f) *sink = s;  // the chains stay positive: never taken
+}
+
+}  // namespace
+
+extern "C" int nbfd_diag_fp32_rate(int packed, int blocks_per_sm, long long iters, double *tflops,
+                                   double *ms, void *stream_) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1 || iters > (1LL << 30) || !tflops)
+    return set_error(NBFD_EINVAL, "blocks_per_sm in [1, 8], iters in [1, 2^30], tflops != NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream_);
+  float *sink = nullptr;
+  if (int st = check_cuda(cudaMallocAsync(reinterpret_cast<void **>(&sink), 4, s), "cudaMallocAsync"))
+    return st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int st = check_cuda(cudaEventCreate(&a), "cudaEventCreate");
+  if (!st) st = check_cuda(cudaEventCreate(&b), "cudaEventCreate");
+  const int grid = sm_count() * blocks_per_sm;
+  if (!st) {
+    // one launch to warm up the clocks and the instruction cache, then the timed one
+    for (int rep = 0; rep < 2 && !st; ++rep) {
+      if (rep == 1) cudaEventRecord(a, s);
+      if (packed)
+        k_fma_rate<true><<<grid, kFmaThreads, 0, s>>>(iters, 0.9999999f, 1e-7f, sink);
+      else
+        k_fma_rate<false><<<grid, kFmaThreads, 0, s>>>(iters, 0.9999999f, 1e-7f, sink);
+      st = check_cuda(cudaGetLastError(), "FMA-rate kernel");
+    }
+    if (!st) cudaEventRecord(b, s);
+  }
+  float t = 0.0f;
+  if (!st) st = check_cuda(cudaEventSynchronize(b), "cudaEventSynchronize");
+  if (!st) st = check_cuda(cudaEventElapsedTime(&t, a, b), "cudaEventElapsedTime");
+  cudaFreeAsync(sink, s);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st) return st;
+  const double fma = (double)grid * kFmaThreads * kFmaChains * (packed ? 2.0 : 1.0) * (double)iters;
+  *tflops = 2.0 * fma / (t * 1e-3) / 1e12;
+  if (ms) *ms = t;
+  return NBFD_OK;
+}
