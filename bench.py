@@ -86,12 +86,16 @@ def parse():
                     help="steps of the uneven five-code batch leg (0: skip)")
     ap.add_argument("--gf64-steps", type=int, default=2,
                     help="timed steps per point of the GF(64) N=1200 plain batched sweep (0: skip)")
+    ap.add_argument("--fused-steps", type=int, default=3,
+                    help="timed steps of the fused vs per-iteration GF(16) comparison (0: skip)")
     ap.add_argument("--prof-steps", type=int, default=8,
                     help="leading steps of the timed region with per-launch kernel timers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=16384, help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-load", type=float, default=30000.0, help="Poisson offered load, frames/s")
     ap.add_argument("--serve-sweep", action="store_true", help="serving sweep over loads and the code mix")
+    ap.add_argument("--serve-mix-loads", type=float, nargs="*", default=[1e4, 1e5],
+                    help="offered loads (frames/s) of the five-code serving mix in the default run")
     return ap.parse_args()
 
 
@@ -273,6 +277,40 @@ def fp32_peak(nb):
     return out
 
 
+def fused_leg(nb, torch, dev, steps, max_iter, F=8192):
+    """The uneven batch's GF(16) (2,4) N=96 group alone (8192 frames, per-frame Eb/N0 uniform in
+    1.0-3.5 dB): nbfd_decode with the fused small-code kernel (each frame's messages in shared
+    memory for all its iterations) against the per-iteration kernels (NBFD_UNFUSED), device time
+    from CUDA events, and the message bytes the per-iteration path streams (36 N q per
+    frame-iteration) that the fused launch keeps on chip."""
+    c = synth.named_code("gf16_n96_k4")
+    enc = synth.Encoder(c)
+    code = nb.Code(c)
+    rng = synth.rng_for(97, 0, 11)
+    _, llr = synth.frames(c, F, rng.uniform(1.0, 3.5, size=F), snr_idx=0, batch_idx=11, encoder=enc)
+    x = torch.from_numpy(llr).to(dev)
+    bits = enc.info_symbols * c["m"]
+    stream = torch.cuda.current_stream()
+    out = {"code": "gf16_n96_k4", "frames": F, "max_iter": max_iter}
+    for name, form in (("fused", FORMS["fwht"]), ("per_iteration", FORMS["fwht"] | nb.UNFUSED)):
+        sym, ok, it = nb.decode(code, x, max_iter, form)  # warm (and the outputs' buffers)
+        need = nb.nbfd_decode_workspace_size(code.handle, F, max_iter, form)
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            ev[i][0].record(stream)
+            nb.nbfd_decode(code.handle, F, x, max_iter, form, sym.data_ptr(), ok, it, ws, need, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / steps
+        out[name] = {"ms_per_step": ms, "mbit_s": bits * F / (ms / 1e3) / 1e6,
+                     "mean_iterations": float(it.float().mean()), "decoded_frac": float(ok.float().mean())}
+    fi = out["per_iteration"]["mean_iterations"] * F
+    out["unfused_message_bytes_per_step"] = fi * 36 * c["N"] * (1 << c["m"])
+    out["speedup"] = out["per_iteration"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    return out
+
+
 GF64_POINTS = (1.0, 1.5, 2.0, 2.5, 3.0)
 
 
@@ -375,12 +413,17 @@ def uneven_leg(nb, torch, dev, form, steps, max_iter):
         res[name] = {"ms_per_step": ms, "mbit_s": bits / (ms / 1e3) / 1e6}
     oks = [float(o[1].float().mean()) for o in outs]
     its = [float(o[2].float().mean()) for o in outs]
-    tunes = [nb.nbfd_autotune_result(h, n, form) for h, n in zip(handles, ns)]
+    tunes = []
+    for h, n in zip(handles, ns):
+        try:
+            tunes.append(nb.nbfd_autotune_result(h, n, form))
+        except nb.NbfdError:  # a group decoded by the fused small-code kernel has no shapes
+            tunes.append(None)
     return {"codes": [n for n, _ in UNEVEN], "frames": ns, "info_bits_per_step": bits,
             "value": res["batch"]["mbit_s"], "unit": "Mbit/s", "ms_per_step": res["batch"]["ms_per_step"],
             "per_code_calls": res["per_code"], "steps": steps, "decoded_frac": oks, "mean_iterations": its,
             "tuned_shapes": [{"check_warps": t[0], "check_stages": t[1], "check_blocks_per_sm": t[2],
-                              "var_blocks_per_sm": t[3]} for t in tunes],
+                              "var_blocks_per_sm": t[3]} if t else "fused small-code kernel" for t in tunes],
             "ebn0_db": "per frame U[1.0, 3.5]", "max_iter": max_iter}
 
 
@@ -447,9 +490,42 @@ def serve_summary(got, wall, phases, offered=None):
             "wall_s": wall, "worker_s": {k: round(v, 4) for k, v in phases.items()}}
 
 
+SERVE_MIX = [("gf16_n96_k4", 0.1), ("gf64_n1200_k6", 0.3), ("gf64_n4096_k8", 0.2), ("gf256_n512_k4", 0.3),
+             ("gf256_n2048_k16", 0.1)]
+
+
+def serve_mix_codes(nb):
+    codes = {}
+    for name, _ in SERVE_MIX:
+        c = synth.named_code(name)
+        enc = synth.Encoder(c)
+        codes[name] = (c, nb.Code(c), enc.info_symbols * c["m"], enc)
+    return codes
+
+
+def serve_mix_point(nb, codes, form, lam, dur):
+    """One offered load of the serving configuration: Poisson arrivals at lam frames/s for dur s,
+    each request a single frame of one of five codes (weights .1/.3/.2/.3/.1), per-request Eb/N0
+    uniform in 1.5-3.5 dB, max 100 iterations, a 40 GB budget for resident messages."""
+    rng = synth.rng_for(17, int(lam))
+    n_req = int(lam * dur)
+    arr = np.sort(rng.uniform(0.0, dur, size=n_req))
+    which = rng.choice(len(SERVE_MIX), size=n_req, p=[w for _, w in SERVE_MIX])
+    streams = []
+    for ci, (name, _) in enumerate(SERVE_MIX):
+        sel = np.nonzero(which == ci)[0]
+        if len(sel) == 0:
+            continue
+        c, code, bits, enc = codes[name]
+        ebn0 = rng.uniform(1.5, 3.5, size=len(sel))
+        _, llr = synth.frames(c, len(sel), ebn0, snr_idx=ci, batch_idx=int(lam) % 100000, encoder=enc)
+        streams.append((code, llr, arr[sel], 100, bits))
+    got, wall, ph = serve_run(nb, streams, form, 40 << 30)
+    return serve_summary(got, wall, ph, lam)
+
+
 def run_serve_sweep(a):
-    """Serving sweep of the configured mix: Poisson arrivals drawn from five codes (weights
-    .1/.3/.2/.3/.1), per-request Eb/N0 uniform in 1.5-3.5 dB, max 100 iterations."""
+    """Serving sweep of the configured mix over offered loads 1e4 .. 1e6 frames/s."""
     import torch
 
     import paper_1008_4370_gb300 as nb
@@ -457,31 +533,11 @@ def run_serve_sweep(a):
 
     nbuild.build()
     torch.cuda.init()
-    mix = [("gf16_n96_k4", 0.1), ("gf64_n1200_k6", 0.3), ("gf64_n4096_k8", 0.2), ("gf256_n512_k4", 0.3),
-           ("gf256_n2048_k16", 0.1)]
-    codes = {}
-    for name, _ in mix:
-        c = synth.named_code(name)
-        enc = synth.Encoder(c)
-        codes[name] = (c, nb.Code(c), enc.info_symbols * c["m"], enc)
+    codes = serve_mix_codes(nb)
+    form = FORMS[a.form] if FORMS[a.form] in (0, 3) else FORMS["fwht"]
     for lam in [1e4, 3e4, 1e5, 3e5, 1e6]:
         dur = min(1.0, max(0.2, 20000.0 / lam))
-        rng = synth.rng_for(17, int(lam))
-        n_req = int(lam * dur)
-        arr = np.sort(rng.uniform(0.0, dur, size=n_req))
-        which = rng.choice(len(mix), size=n_req, p=[w for _, w in mix])
-        streams = []
-        for ci, (name, _) in enumerate(mix):
-            sel = np.nonzero(which == ci)[0]
-            if len(sel) == 0:
-                continue
-            c, code, bits, enc = codes[name]
-            ebn0 = rng.uniform(1.5, 3.5, size=len(sel))
-            _, llr = synth.frames(c, len(sel), ebn0, snr_idx=ci, batch_idx=int(lam) % 100000, encoder=enc)
-            streams.append((code, llr, arr[sel], 100, bits))
-        got, wall, ph = serve_run(nb, streams, FORMS[a.form] if FORMS[a.form] in (0, 3) else FORMS["fwht"],
-                                  40 << 30)
-        print(json.dumps({"serving_sweep": serve_summary(got, wall, ph, lam), "form": a.form}), flush=True)
+        print(json.dumps({"serving_sweep": serve_mix_point(nb, codes, form, lam, dur), "form": a.form}), flush=True)
 
 
 def run_ours(a):
@@ -667,10 +723,16 @@ def run_ours(a):
         got2, wall2, ph2 = serve_run(nb, [(code, llr_req, arr, a.max_iter, info_bits)], form, 32 << 30)
         ld = serve_summary(got2, wall2, ph2, a.serve_load)
         served = {"form": a.form, "saturation": sat, "poisson": ld}
+        if a.serve_mix_loads:
+            # the configured five-code mix at a few offered loads (the full sweep: --serve-sweep)
+            codes_mix = serve_mix_codes(nb)
+            served["mix"] = [serve_mix_point(nb, codes_mix, form, lam, min(1.0, max(0.2, 10000.0 / lam)))
+                             for lam in a.serve_mix_loads]
     peaks, peak_kind = load_peaks()
     gf64 = None
     if a.gf64_steps > 0 and world == 1:
         gf64 = gf64_leg(nb, torch, dev, a.gf64_steps, a.max_iter, float(peaks["hbm_gbs"]))
+    fused = fused_leg(nb, torch, dev, a.fused_steps, a.max_iter) if a.fused_steps > 0 and world == 1 else None
     fp32 = fp32_peak(nb) if rank == 0 else None
     # the uneven five-code batch last: it holds about 9 GB while it runs
     uneven = None
@@ -755,6 +817,7 @@ def run_ours(a):
         "store16": store16,
         "uneven_batch": uneven,
         "plain_batch_gf64": gf64,
+        "fused_gf16": fused,
         "fp32_peak": fp32,
         "served": served,
         "gpu_launches": launches_total,

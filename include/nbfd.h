@@ -67,6 +67,13 @@ extern "C" {
  * Error added per stored entry: |d ln|P|| <= 2^-11 |ln|P||, i.e. |dP| <= 2^-11 / e. Supported
  * with NBFD_FORM_FP32_FWHT at m = 8 (other combinations give NBFD_ENOTSUP); not by the server. */
 #define NBFD_STORE_F16 0x200
+/* Path flag, OR'ed into a form: decode GF(16) codes with the per-iteration kernels (one check,
+ * variable-node and stop launch per iteration over every active frame) even where the fused
+ * small-code kernel applies. Without it, nbfd_decode and nbfd_decode_batch decode the frames of a
+ * GF(16) code whose per-frame messages fit in shared memory (the FWHT form, float storage) in one
+ * launch that keeps each frame on chip for all of its iterations; both paths give bit-identical
+ * outputs. The paper has no counterpart (it is a choice of schedule, not of arithmetic). */
+#define NBFD_UNFUSED 0x400
 
 typedef struct nbfd_code nbfd_code; /* opaque, library-owned, immutable after creation */
 
@@ -353,12 +360,13 @@ void nbfd_srv_destroy(nbfd_server *srv);
 #define NBFD_KERNEL_VAR 2
 #define NBFD_KERNEL_SYNDROME 3
 #define NBFD_KERNEL_TAIL 4 /* the remaining iterations of the last few frames, one launch */
-#define NBFD_KERNEL_COUNT 5
+#define NBFD_KERNEL_FUSED 5 /* whole decodes of small GF(16) codes, one launch */
+#define NBFD_KERNEL_COUNT 6
 
 /* Time the kernels whose bit (1 << NBFD_KERNEL_*) is set in kernel_mask (0 disables; NBFD_PROF_ALL
- * times all five) for the calling process; resets the totals. Each timed launch adds two event
+ * times all six) for the calling process; resets the totals. Each timed launch adds two event
  * records to the stream. */
-#define NBFD_PROF_ALL 0x1F
+#define NBFD_PROF_ALL 0x3F
 int nbfd_prof_enable(int kernel_mask);
 /* Totals since the last enable: device milliseconds, launches, and frame-units (the sum over
  * launches of the number of frames the launch processed). Any out pointer may be NULL. */

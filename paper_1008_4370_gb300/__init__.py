@@ -19,7 +19,7 @@ __all__ = [
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
-    "STORE_F16", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
+    "STORE_F16", "UNFUSED", "KERNEL_FUSED", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
     "nbfd_diag_preset_status", "nbfd_diag_fp32_rate",
     "nbfd_last_decode_stats",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
@@ -36,7 +36,7 @@ FORM_FP32_TC = 4
 DECIDE_SYMBOL = 0x100  # OR into a form: symbol-MAP tentative decisions
 SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT, FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)
 TC_FORMS = (FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)  # need m = 8
-KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME, KERNEL_TAIL = 0, 1, 2, 3, 4
+KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME, KERNEL_TAIL, KERNEL_FUSED = 0, 1, 2, 3, 4, 5
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libnbfd.so")
@@ -198,6 +198,7 @@ def nbfd_decode(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, ite
 
 BATCH_AUTOTUNE = 1
 STORE_F16 = 0x200  # form flag: messages stored as IEEE half (FWHT form, m = 8)
+UNFUSED = 0x400  # form flag: per-iteration kernels even where the fused GF(16) kernel applies
 
 
 def nbfd_last_decode_stats():
@@ -378,7 +379,7 @@ def nbfd_srv_destroy(srv):
 
 
 def nbfd_prof_enable(kernel_mask: int):
-    """Time the kernels whose bit (1 << KERNEL_*) is set; 0 disables, 0x1F times all."""
+    """Time the kernels whose bit (1 << KERNEL_*) is set; 0 disables, 0x3F times all."""
     _check(lib().nbfd_prof_enable(int(kernel_mask)))
 
 

@@ -246,18 +246,30 @@ int decode_loop(const nbfd_code *c, int F, const float *llr, int max_iter, int f
     // per edge -- half the INITIALIZATION's writes (for q >= 64, where a vector is one bulk copy
     // of at least 256 bytes).
     const float *lambda0 = !f16 && F > tail_max && c->q >= 64 ? w.v2c : nullptr;
-    tm.begin(NBFD_KERNEL_INIT, 0, s);
-    if ((st = check_cuda(launch_init(c, F, llr, lambda0 ? w.v2c : nullptr,
-                                     lambda0 ? nullptr : w.v2c, w.list[1], w.count + 1, s, f16),
-                         "init kernel")))
-      break;
-    tm.end(s);
+    // Small GF(16) codes: every frame decoded start to finish in one launch, its messages kept
+    // in shared memory (bit-identical to the per-iteration path below)
+    const bool fused = fused_small_applies(c, form);
+    if (fused) {
+      tm.begin(NBFD_KERNEL_FUSED, 0, s);
+      if ((st = check_cuda(launch_fused_small(c, F, llr, symbols, ok, iters, w.stats, max_iter,
+                                              symbol, s),
+                           "fused small-code kernel")))
+        break;
+      tm.end(s);
+    } else {
+      tm.begin(NBFD_KERNEL_INIT, 0, s);
+      if ((st = check_cuda(launch_init(c, F, llr, lambda0 ? w.v2c : nullptr,
+                                       lambda0 ? nullptr : w.v2c, w.list[1], w.count + 1, s, f16),
+                           "init kernel")))
+        break;
+      tm.end(s);
+    }
     // The host reads the active-frame count every few iterations; in between it queues
     // iterations blindly (a launch with no active frame returns at once) and sizes each grid by
     // the last count it read, an upper bound since counts only shrink. With the tail kernel the
     // count is read every 4 iterations, so that the switch to it comes early; without it, every
     // 16 once few frames are left (a host round trip then costs as much as several iterations).
-    long long active = F;
+    long long active = fused ? 0 : F;
     int it = 1;
     while (st == NBFD_OK && it <= max_iter && active > 0) {
       if (active <= tail_max) {

@@ -302,6 +302,10 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
     }
   }
   std::vector<TuneVal> tune(n);
+  // groups of small GF(16) codes decode start to finish in one fused launch each, on their own
+  // branch stream beside the graph replays of the other groups
+  std::vector<char> fused(n, 0);
+  for (int i = 0; i < n; ++i) fused[i] = n_frames[i] > 0 && fused_small_applies(codes[i], form);
   int32_t *host = pinned_counts();
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -322,6 +326,10 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
     // INITIALIZATION (list 1 = all frames, count 1 = F), launch shapes
     for (int i = 0; i < n && !st; ++i) {
       if (n_frames[i] == 0) continue;
+      if (fused[i]) {  // its launch writes every output; only the state words start at 0
+        st = check_cuda(cudaMemsetAsync(ws[i].state, 0, 256, s), "cudaMemsetAsync");
+        continue;
+      }
       if ((st = init_code(i))) break;
       if (!tune_lookup(codes[i], n_frames[i], form, &tune[i].check, &tune[i].var) &&
           (flags & NBFD_BATCH_AUTOTUNE)) {
@@ -354,6 +362,17 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
     if ((st = check_cuda(cudaEventRecord(events[n + 1], s), "cudaEventRecord")) ||
         (st = check_cuda(cudaStreamWaitEvent(cs, events[n + 1], 0), "cudaStreamWaitEvent")))
       break;
+    for (int i = 0; i < n && !st; ++i) {
+      if (!fused[i]) continue;
+      if ((st = check_cuda(cudaStreamWaitEvent(br[i], events[n + 1], 0), "cudaStreamWaitEvent")))
+        break;
+      st = check_cuda(launch_fused_small(codes[i], n_frames[i], llr[i], symbols[i], ok[i], iters[i],
+                                         ws[i].state + 16, max_iter,
+                                         (form & NBFD_DECIDE_SYMBOL) != 0, br[i]),
+                      "fused small-code kernel");
+      if (!st) st = check_cuda(cudaEventRecord(events[i], br[i]), "cudaEventRecord");
+    }
+    if (st) break;
     if ((st = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed),
                          "cudaStreamBeginCapture")))
       break;
@@ -362,6 +381,7 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
       const nbfd_code *c = codes[i];
       const int F = n_frames[i];
       cudaStream_t b = br[i];
+      if (fused[i]) continue;
       ce = cudaStreamWaitEvent(b, events[n], 0);
       for (int p = 1; p >= 0 && ce == cudaSuccess && F > 0; --p) {
         FrameSet fs;
@@ -403,8 +423,12 @@ extern "C" int nbfd_decode_batch(int n, const nbfd_code *const *codes, const int
       if (st) break;
       if ((st = check_cuda(cudaStreamSynchronize(cs), "cudaStreamSynchronize"))) break;
       active = 0;
-      for (int i = 0; i < n; ++i) active += n_frames[i] > 0 ? host[i] : 0;
+      for (int i = 0; i < n; ++i) active += n_frames[i] > 0 && !fused[i] ? host[i] : 0;
     }
+    if (st) break;
+    // the fused groups' launches
+    for (int i = 0; i < n && !st; ++i)
+      if (fused[i]) st = check_cuda(cudaStreamWaitEvent(cs, events[i], 0), "cudaStreamWaitEvent");
     if (st) break;
     for (int i = 0; i < n && !st; ++i)
       st = check_cuda(cudaMemcpyAsync(host + kMaxCodes + i, ws[i].state + 17, 4,

@@ -388,7 +388,7 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
 }
 
 bool form_supported(int form, int m) {
-  if (form & ~(0xff | NBFD_DECIDE_SYMBOL | NBFD_STORE_F16)) return false;
+  if (form & ~(0xff | NBFD_DECIDE_SYMBOL | NBFD_STORE_F16 | NBFD_UNFUSED)) return false;
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
   if (stores_f16(form)) return (form & 0xff) == NBFD_FORM_FP32_FWHT && m == 8;
   switch (form & 0xff) {

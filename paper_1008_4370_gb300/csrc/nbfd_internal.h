@@ -155,6 +155,16 @@ cudaError_t launch_tail_x2(const nbfd_code *c, FrameSet fs, const float *llr, fl
                            float *c2v, uint16_t *sym, uint8_t *fsyn, int it0, int max_iter,
                            uint8_t *ok, int32_t *iters, int32_t *stats, cudaStream_t s,
                            bool symbol);
+// Small GF(16) codes (FWHT form, float storage, per-frame messages within 96 KiB of shared
+// memory): the INITIALIZATION and every iteration of each frame in one launch, the frame's
+// messages kept in shared memory (kernels_fused_small.cu). ok[f], iters[f] and sym[f] as
+// nbfd_decode writes them; stats[0] counts the Fourier-only clears, stats[2] is the launch's
+// frame counter: stats[0] and stats[2] must be 0 when it starts.
+bool fused_small_applies(const nbfd_code *c, int form);
+size_t fused_small_smem(const nbfd_code *c);
+cudaError_t launch_fused_small(const nbfd_code *c, int F, const float *llr, uint16_t *sym,
+                               uint8_t *ok, int32_t *iters, int32_t *stats, int max_iter,
+                               bool symbol, cudaStream_t s);
 // GF(256) only: the same computation with two variables per warp, 16 entries per lane, one
 // shared-memory transpose per transform and packed f32x2 butterflies
 cudaError_t launch_var_fwht8x2(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,

@@ -97,8 +97,12 @@ def test_uneven_batch_full_config_with_autotune(dev):
     torch.cuda.synchronize()
     for (c, tx, _), code, (sym, ok, it) in zip(groups, codes, outs):
         F = tx.shape[0]
-        shape = nb.nbfd_autotune_result(code.handle, F, nb.FORM_FP32_FWHT)
-        assert 1 <= shape[0] <= 8 and shape[1] >= 3 and shape[2] >= 1 and shape[3] >= 1
+        if c["m"] == 4:  # the GF(16) group runs as one fused launch: no shapes to tune
+            with pytest.raises(nb.NbfdError):
+                nb.nbfd_autotune_result(code.handle, F, nb.FORM_FP32_FWHT)
+        else:
+            shape = nb.nbfd_autotune_result(code.handle, F, nb.FORM_FP32_FWHT)
+            assert 1 <= shape[0] <= 8 and shape[1] >= 3 and shape[2] >= 1 and shape[3] >= 1
         ex = torch.empty((F, code.M), dtype=torch.int16, device=dev)
         nb.nbfd_syndrome(code.handle, F, sym, None, None, ex)
         torch.cuda.synchronize()
