@@ -88,6 +88,8 @@ def parse():
                     help="timed steps per point of the GF(64) N=1200 plain batched sweep (0: skip)")
     ap.add_argument("--fused-steps", type=int, default=3,
                     help="timed steps of the fused vs per-iteration GF(16) comparison (0: skip)")
+    ap.add_argument("--table1-reps", type=int, default=3,
+                    help="timed launches per kernel of the Log-SP vs Log-Fourier comparison (0: skip)")
     ap.add_argument("--prof-steps", type=int, default=8,
                     help="leading steps of the timed region with per-launch kernel timers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -308,6 +310,50 @@ def fused_leg(nb, torch, dev, steps, max_iter, F=8192):
     fi = out["per_iteration"]["mean_iterations"] * F
     out["unfused_message_bytes_per_step"] = fi * 36 * c["N"] * (1 << c["m"])
     out["speedup"] = out["per_iteration"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    return out
+
+
+def table1_leg(nb, torch, dev, reps, F=1024, ebn0=1.5):
+    """Table 1 of the paper on the GPU: per-launch device time of the check node and of the
+    variable node for conventional Log-SP (Section 2.2: (k-1)-fold log-convolutions at the check,
+    additions at the variable) against Log-Fourier SP (Section 3.2: additions at the check,
+    2-fold convolutions at the degree-2 variable; FWHT and direct forms), 1024 frames of GF(256)
+    (2,4) N=512, first-iteration inputs. CUDA events on the launching stream, mean of reps."""
+    c = synth.named_code(CODE_NAME)
+    code = nb.Code(c)
+    N, E, q, m, k = c["N"], 2 * c["N"], 1 << c["m"], c["m"], c["k"]
+    M = E // k
+    _, llr = synth.frames(c, F, ebn0, snr_idx=0, batch_idx=31)
+    x = torch.from_numpy(llr).to(dev)
+    a = torch.empty((F, E, q), dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    sym = torch.empty((F, N), dtype=torch.int16, device=dev)
+    fsyn = torch.empty((F, E), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for i in range(reps):
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(s_.elapsed_time(e_) for s_, e_ in ev) / reps
+
+    out = {"code": CODE_NAME, "frames": F, "ebn0_db": ebn0, "reps": reps}
+    nb.nbfd_logsp_init(code.handle, F, x, a)
+    lsp_check = timed(lambda: nb.nbfd_logsp_check_update(code.handle, F, a, b))
+    lsp_var = timed(lambda: nb.nbfd_logsp_var_update(code.handle, F, x, b, a, sym))
+    out["log_sp"] = {"check_ms": lsp_check, "var_ms": lsp_var,
+                     "check_fma_per_frame": 3 * (k - 2) * M * q * q, "var_adds_per_frame": 3 * N * q}
+    nb.nbfd_init_messages(code.handle, F, x, None, a)
+    lf_check = timed(lambda: nb.nbfd_check_update(code.handle, F, a, b))
+    out["log_fourier"] = {"check_ms": lf_check, "check_adds_per_frame": 3 * k * M * q}
+    for fname in ("fwht", "direct"):
+        ms = timed(lambda: nb.nbfd_var_update(code.handle, F, FORMS[fname], x, b, a, sym, fsyn))
+        out["log_fourier"][f"var_{fname}_ms"] = ms
+    out["log_fourier"]["var_direct_fma_per_frame"] = E * q * q + 3 * m * q * N
     return out
 
 
@@ -734,6 +780,7 @@ def run_ours(a):
         gf64 = gf64_leg(nb, torch, dev, a.gf64_steps, a.max_iter, float(peaks["hbm_gbs"]))
     fused = fused_leg(nb, torch, dev, a.fused_steps, a.max_iter) if a.fused_steps > 0 and world == 1 else None
     fp32 = fp32_peak(nb) if rank == 0 else None
+    table1 = table1_leg(nb, torch, dev, a.table1_reps) if a.table1_reps > 0 and world == 1 else None
     # the uneven five-code batch last: it holds about 9 GB while it runs
     uneven = None
     if a.uneven_steps > 0 and world == 1 and (form & 0xff) in (FORMS["fwht"], FORMS["direct"]):
@@ -818,6 +865,7 @@ def run_ours(a):
         "uneven_batch": uneven,
         "plain_batch_gf64": gf64,
         "fused_gf16": fused,
+        "table1_check_vs_var": table1,
         "fp32_peak": fp32,
         "served": served,
         "gpu_launches": launches_total,

@@ -372,6 +372,34 @@ int nbfd_prof_enable(int kernel_mask);
  * launches of the number of frames the launch processed). Any out pointer may be NULL. */
 int nbfd_prof_get(int kernel, double *ms, long long *launches, long long *frame_units);
 
+/* ---- conventional Log-SP (Section 2.2), the decoder Log-Fourier SP reformulates ------------
+ * Kept to measure Table 1 on the GPU: its check node carries the log-convolutions, its variable
+ * node only component-wise additions. Messages are x-domain log-probabilities lambda(x) in
+ * [-inf, 0] as float32 (no sign bit), [F][slot][x] with the check-major slots of the code; m in
+ * [3, 8]. No decoding loop: the calls are one step each over every frame, like the step-level
+ * calls above. Errors: NBFD_EINVAL, NBFD_ENOTSUP, NBFD_ECUDA. */
+
+/* INITIALIZATION: lambda_vc = lambda0_v(x) = ln Pr(X_v = x | y_v) = sum_i ln Pr(b_i = x_i | L_i)
+ * on both edges of every variable. llr_dev [F][N][m] in, v2c_dev [F][E][q] out. */
+int nbfd_logsp_init(const nbfd_code *code, int n_frames, const float *llr_dev, float *v2c_dev,
+                    void *cuda_stream);
+
+/* CHECK TO VARIABLE (the log-convolution of Section 2.2): lambda~_vc(x) = lambda_vc(h^{-1} x);
+ * lambda~_cv = the log-convolution of the other k - 1 lambda~_v'c (computed as linear XOR
+ * convolutions of their max-shifted exponentials, prefix and suffix products); lambda_cv(x) =
+ * lambda~_cv(h x), normalised to max_x lambda_cv(x) = 0. Needs k >= 3. v2c_dev in, c2v_dev out
+ * ([F][E][q], must not alias). */
+int nbfd_logsp_check_update(const nbfd_code *code, int n_frames, const float *v2c_dev,
+                            float *c2v_dev, void *cuda_stream);
+
+/* VARIABLE TO CHECK and TENTATIVE DECISION: lambda_vc = lambda0_v + lambda_c'v (c' the other
+ * check of v) normalised to lambda_vc(0) = 0 (to the maximum where lambda_vc(0) = -inf);
+ * symbols_dev [F][N] (may be NULL) = argmax_x lambda0_v + lambda_c1v + lambda_c2v, ties to the
+ * lowest x. */
+int nbfd_logsp_var_update(const nbfd_code *code, int n_frames, const float *llr_dev,
+                          const float *c2v_dev, float *v2c_dev, uint16_t *symbols_dev,
+                          void *cuda_stream);
+
 /* ---- diagnostics (no counterpart in the paper) ----------------------------------------------
  * nbfd_diag_wait_expiry -- run the expiry path of the bounded device-side waits on purpose: one
  * thread waits, with the kernels' bounded mbarrier wait and a budget of budget_cycles SM cycles

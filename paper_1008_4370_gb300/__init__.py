@@ -20,7 +20,8 @@ __all__ = [
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
     "STORE_F16", "UNFUSED", "KERNEL_FUSED", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
-    "nbfd_diag_preset_status", "nbfd_diag_fp32_rate",
+    "nbfd_diag_preset_status", "nbfd_diag_fp32_rate", "nbfd_logsp_init", "nbfd_logsp_check_update",
+    "nbfd_logsp_var_update",
     "nbfd_last_decode_stats",
     "nbfd_check_update", "nbfd_var_update", "nbfd_syndrome", "nbfd_prof_enable", "nbfd_prof_get",
     "nbfd_last_error", "nbfd_status_string", "Code", "decode", "nbfd_srv_create", "nbfd_srv_submit",
@@ -61,6 +62,9 @@ SIGNATURES = [
     ("nbfd_diag_wait_expiry", _I, [ctypes.c_longlong, _P]),
     ("nbfd_diag_preset_status", _I, [ctypes.c_int32]),
     ("nbfd_diag_fp32_rate", _I, [_I, _I, ctypes.c_longlong, _P, _P, _P]),
+    ("nbfd_logsp_init", _I, [_P, _I, _P, _P, _P]),
+    ("nbfd_logsp_check_update", _I, [_P, _I, _P, _P, _P]),
+    ("nbfd_logsp_var_update", _I, [_P, _I, _P, _P, _P, _P, _P]),
     ("nbfd_last_decode_stats", _I, [_P]),
     ("nbfd_check_update_f16", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P]),
@@ -220,6 +224,27 @@ def nbfd_diag_fp32_rate(packed=0, blocks_per_sm=4, iters=1 << 20, stream=None):
     _check(lib().nbfd_diag_fp32_rate(int(packed), int(blocks_per_sm), int(iters), ctypes.byref(t),
                                      ctypes.byref(ms), _stream(stream)))
     return t.value, ms.value
+
+
+def nbfd_logsp_init(handle, n_frames, llr, v2c, stream=None):
+    """Conventional Log-SP INITIALIZATION (Section 2.2): lambda0 on both edges of every variable."""
+    import torch
+    _check(lib().nbfd_logsp_init(handle, int(n_frames), _dptr(llr, torch.float32), _dptr(v2c, torch.float32),
+                                 _stream(stream)))
+
+
+def nbfd_logsp_check_update(handle, n_frames, v2c, c2v, stream=None):
+    """Conventional Log-SP CHECK TO VARIABLE: the log-convolution of the other k - 1 messages."""
+    import torch
+    _check(lib().nbfd_logsp_check_update(handle, int(n_frames), _dptr(v2c, torch.float32),
+                                         _dptr(c2v, torch.float32), _stream(stream)))
+
+
+def nbfd_logsp_var_update(handle, n_frames, llr, c2v, v2c, symbols=None, stream=None):
+    """Conventional Log-SP VARIABLE TO CHECK + argmax TENTATIVE DECISION."""
+    import torch
+    _check(lib().nbfd_logsp_var_update(handle, int(n_frames), _dptr(llr, torch.float32), _dptr(c2v, torch.float32),
+                                       _dptr(v2c, torch.float32), _dptr(symbols), _stream(stream)))
 
 
 def nbfd_diag_preset_status(value):

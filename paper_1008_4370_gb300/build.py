@@ -22,7 +22,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libnbfd.so")
 
 SOURCES = ["code.cpp", "kernels.cu", "kernels_check.cu", "kernels_var_fwht.cu", "kernels_var_fwht8x2.cu", "kernels_var_fwht6x8.cu",
-           "kernels_var_fwht4.cu", "kernels_fused_small.cu",
+           "kernels_var_fwht4.cu", "kernels_fused_small.cu", "kernels_logsp.cu",
            "kernels_var_tc.cu",
            "decode.cu", "decode_noalloc.cu", "decode_batch.cu", "server.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

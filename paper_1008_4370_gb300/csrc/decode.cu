@@ -457,3 +457,42 @@ extern "C" int nbfd_syndrome(const nbfd_code *c, int F, const uint16_t *symbols,
                                     static_cast<cudaStream_t>(stream)),
                     "syndrome kernel");
 }
+
+// ---- conventional Log-SP (Section 2.2), step by step --------------------------------------
+
+extern "C" int nbfd_logsp_init(const nbfd_code *c, int F, const float *llr, float *v2c,
+                               void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (!logsp_supported(c->m)) return set_error(NBFD_ENOTSUP, "Log-SP needs m in [3, 8]");
+  if (F == 0) return NBFD_OK;
+  if (!llr || !v2c) return set_error(NBFD_EINVAL, "NULL buffer");
+  if (int st = check_device(c)) return st;
+  return check_cuda(launch_logsp_var(c, F, llr, nullptr, v2c, nullptr, true,
+                                     static_cast<cudaStream_t>(stream)),
+                    "Log-SP initialization kernel");
+}
+
+extern "C" int nbfd_logsp_check_update(const nbfd_code *c, int F, const float *v2c, float *c2v,
+                                       void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (!logsp_supported(c->m) || c->k < 3)
+    return set_error(NBFD_ENOTSUP, "Log-SP check node needs m in [3, 8] and k >= 3");
+  if (F == 0) return NBFD_OK;
+  if (!v2c || !c2v || v2c == c2v) return set_error(NBFD_EINVAL, "bad message buffers");
+  if (int st = check_device(c)) return st;
+  return check_cuda(launch_logsp_check(c, F, v2c, c2v, static_cast<cudaStream_t>(stream)),
+                    "Log-SP check kernel");
+}
+
+extern "C" int nbfd_logsp_var_update(const nbfd_code *c, int F, const float *llr,
+                                     const float *c2v, float *v2c, uint16_t *symbols,
+                                     void *stream) {
+  if (!c || F < 0) return set_error(NBFD_EINVAL, "bad argument");
+  if (!logsp_supported(c->m)) return set_error(NBFD_ENOTSUP, "Log-SP needs m in [3, 8]");
+  if (F == 0) return NBFD_OK;
+  if (!llr || !c2v || !v2c || v2c == c2v) return set_error(NBFD_EINVAL, "bad buffers");
+  if (int st = check_device(c)) return st;
+  return check_cuda(launch_logsp_var(c, F, llr, c2v, v2c, symbols, false,
+                                     static_cast<cudaStream_t>(stream)),
+                    "Log-SP variable kernel");
+}

@@ -165,6 +165,13 @@ size_t fused_small_smem(const nbfd_code *c);
 cudaError_t launch_fused_small(const nbfd_code *c, int F, const float *llr, uint16_t *sym,
                                uint8_t *ok, int32_t *iters, int32_t *stats, int max_iter,
                                bool symbol, cudaStream_t s);
+// Conventional Log-SP of Section 2.2 (kernels_logsp.cu), m = 3..8: the check node's log-
+// convolutions and the variable node's additions, x-domain log-probability messages.
+bool logsp_supported(int m);
+cudaError_t launch_logsp_check(const nbfd_code *c, int F, const float *v2c, float *c2v,
+                               cudaStream_t s);
+cudaError_t launch_logsp_var(const nbfd_code *c, int F, const float *llr, const float *c2v,
+                             float *v2c, uint16_t *sym, bool init, cudaStream_t s);
 // GF(256) only: the same computation with two variables per warp, 16 entries per lane, one
 // shared-memory transpose per transform and packed f32x2 butterflies
 cudaError_t launch_var_fwht8x2(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
