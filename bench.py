@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fwht", choices=sorted(FORMS))
     ap.add_argument("--plain-steps", type=int, default=3, help="steps of the plain FP32 direct form")
+    ap.add_argument("--code", default=CODE_NAME,
+                    help="named code of the main decode (the measured workload is GF(256) N=512; other codes "
+                         "serve kernel captures)")
     ap.add_argument("--frames", type=int, default=1024)
     ap.add_argument("--ebn0", type=float, default=1.5)
     ap.add_argument("--max-iter", type=int, default=100)
@@ -469,7 +472,8 @@ def uneven_leg(nb, torch, dev, form, steps, max_iter):
             "value": res["batch"]["mbit_s"], "unit": "Mbit/s", "ms_per_step": res["batch"]["ms_per_step"],
             "per_code_calls": res["per_code"], "steps": steps, "decoded_frac": oks, "mean_iterations": its,
             "tuned_shapes": [{"check_warps": t[0], "check_stages": t[1], "check_blocks_per_sm": t[2],
-                              "var_blocks_per_sm": t[3]} if t else "fused small-code kernel" for t in tunes],
+                              "var_blocks_per_sm": t[3], "var_warps": t[4]} if t else "fused small-code kernel"
+                             for t in tunes],
             "ebn0_db": "per frame U[1.0, 3.5]", "max_iter": max_iter}
 
 
@@ -605,7 +609,7 @@ def run_ours(a):
     nb.lib()
     form = FORMS[a.form]
 
-    code_d = synth.named_code(CODE_NAME)
+    code_d = synth.named_code(a.code)
     enc = synth.Encoder(code_d)
     m, N, E, q = code_d["m"], code_d["N"], 2 * code_d["N"], 1 << code_d["m"]
     info_bits = enc.info_symbols * m
@@ -812,7 +816,7 @@ def run_ours(a):
         }[dom]
         achieved = bytes_per_frame * units / (ms / 1e3) / 1e9
         peak = float(peaks["hbm_gbs"])
-        tpf = measured_traffic(names[dom], a.form, CODE_NAME) if a.frames >= 256 else None
+        tpf = measured_traffic(names[dom], a.form, a.code) if a.frames >= 256 else None
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None if tpf is None else tpf * units / launches,
                 "algorithmic_bytes_per_launch": bytes_per_frame * units / launches,
@@ -826,7 +830,7 @@ def run_ours(a):
     launches_total = int(round(3 * prof[1][1] * a.steps / prof_steps)) + a.steps
 
     cpu = None
-    if world == 1 and not a.no_cpu_baseline:
+    if world == 1 and not a.no_cpu_baseline and a.code == CODE_NAME:
         cores = os.cpu_count() or 1
         sample = batches[0][1][:cores].cpu().numpy()
         wall_c, fi = oracle_frame_iterations(sample, 2, cores)
@@ -850,8 +854,9 @@ def run_ours(a):
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "GF(256) (2,4) N=512, 1024 frames per step, Eb/N0 1.5 dB, random codewords, "
-                               "max 100 iterations, early stop",
+        "config": {"workload": ("GF(256) (2,4) N=512, 1024 frames per step, Eb/N0 1.5 dB, random codewords, "
+                                "max 100 iterations, early stop") if a.code == CODE_NAME and F == 1024 else
+                   f"{a.code}, {F} frames per step, Eb/N0 {a.ebn0} dB, random codewords, max {a.max_iter} iterations",
                    "frames_per_step": F, "ebn0_db": a.ebn0, "max_iter": a.max_iter, "form": a.form,
                    "info_bits_per_frame": info_bits, "design_info_bits": int(N * m * (1 - 2 / code_d["k"])),
                    "l2": "working set > L2 (messages 2 x 1.07 GB streamed every iteration)",

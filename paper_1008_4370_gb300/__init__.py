@@ -67,7 +67,7 @@ SIGNATURES = [
     ("nbfd_logsp_var_update", _I, [_P, _I, _P, _P, _P, _P, _P]),
     ("nbfd_last_decode_stats", _I, [_P]),
     ("nbfd_check_update_f16", _I, [_P, _I, _P, _P, _P]),
-    ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P]),
+    ("nbfd_autotune_result", _I, [_P, _I, _I, _P, _P, _P, _P, _P]),
     ("nbfd_init_messages", _I, [_P, _I, _P, _P, _P, _P]),
     ("nbfd_check_update", _I, [_P, _I, _P, _P, _P]),
     ("nbfd_var_update", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
@@ -293,8 +293,9 @@ def nbfd_autotune(handle, n_frames, form, stream=None):
 
 
 def nbfd_autotune_result(handle, n_frames, form):
-    """(check warps, check stages, check blocks per SM, variable-node blocks per SM)."""
-    v = [ctypes.c_int() for _ in range(4)]
+    """(check warps, check stages, check blocks per SM, variable-node blocks per SM, variable-node
+    warps per block or 0)."""
+    v = [ctypes.c_int() for _ in range(5)]
     _check(lib().nbfd_autotune_result(handle, int(n_frames), int(form), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
 

@@ -102,18 +102,23 @@ int tune_code(const nbfd_code *c, int F, int form, const float *llr, float *v2c,
   }
   if (best_ms < 0.0f) return set_error(NBFD_ECUDA, "autotune: no check-kernel shape ran");
   best_ms = -1.0f;
+  const bool x8 = (form & 0xff) == NBFD_FORM_FP32_FWHT && var_fwht6x8_applies(c);
   const std::vector<int> var_bps =
-      (form & 0xff) == NBFD_FORM_FP32_FWHT && (c->m == 8 || var_fwht6x8_applies(c))
+      (form & 0xff) == NBFD_FORM_FP32_FWHT && (c->m == 8 || x8)
           ? std::vector<int>{1, 2, 3, 4, 8, 16, 32}
           : std::vector<int>{1, 2, 4, 8, 16, 32};
-  for (int bps : var_bps) {
-    VarTune vt{bps};
-    const float ms = time_launches(s, 3, [&] {
-      return launch_var(c, fs, form, llr, c2v, v2c, sym, fsyn, s, nullptr, vt);
-    });
-    if (ms > 0.0f && (best_ms < 0.0f || ms < best_ms)) {
-      best_ms = ms;
-      best.var = vt;
+  // the GF(64) kernel's block shapes: 4 warps (3 blocks per SM), 7 (2), 15 (1)
+  const std::vector<int> var_warps = x8 ? std::vector<int>{4, 7, 15} : std::vector<int>{0};
+  for (int w : var_warps) {
+    for (int bps : var_bps) {
+      VarTune vt{bps, w};
+      const float ms = time_launches(s, 3, [&] {
+        return launch_var(c, fs, form, llr, c2v, v2c, sym, fsyn, s, nullptr, vt);
+      });
+      if (ms > 0.0f && (best_ms < 0.0f || ms < best_ms)) {
+        best_ms = ms;
+        best.var = vt;
+      }
     }
   }
   if (best_ms < 0.0f) return set_error(NBFD_ECUDA, "autotune: no variable-node shape ran");
@@ -236,7 +241,7 @@ extern "C" int nbfd_autotune(const nbfd_code *c, int F, int form, void *stream_)
 
 extern "C" int nbfd_autotune_result(const nbfd_code *c, int F, int form, int *check_warps,
                                     int *check_stages, int *check_blocks_per_sm,
-                                    int *var_blocks_per_sm) {
+                                    int *var_blocks_per_sm, int *var_warps) {
   if (!c) return set_error(NBFD_EINVAL, "code is NULL");
   CheckTune ct;
   VarTune vt;
@@ -245,6 +250,7 @@ extern "C" int nbfd_autotune_result(const nbfd_code *c, int F, int form, int *ch
   if (check_stages) *check_stages = ct.stages;
   if (check_blocks_per_sm) *check_blocks_per_sm = ct.blocks_per_sm;
   if (var_blocks_per_sm) *var_blocks_per_sm = vt.blocks_per_sm;
+  if (var_warps) *var_warps = vt.warps;
   return NBFD_OK;
 }
 

@@ -51,6 +51,7 @@ struct CheckTune {
 };
 struct VarTune {
   int blocks_per_sm = 0;  // grid cap in blocks per SM
+  int warps = 0;          // warps per block where the kernel has several shapes (GF(64): 4, 7, 15)
 };
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 // Waves of resident blocks for a grid-stride kernel with `work` items over `warps_per_wave`
