@@ -358,6 +358,13 @@ def table1_leg(nb, torch, dev, reps, F=1024, ebn0=1.5):
         ms = timed(lambda: nb.nbfd_var_update(code.handle, F, FORMS[fname], x, b, a, sym, fsyn))
         out["log_fourier"][f"var_{fname}_ms"] = ms
     out["log_fourier"]["var_direct_fma_per_frame"] = E * q * q + 3 * m * q * N
+    # the tensor-core forms on both paths: warp-level mma.sync and tcgen05 (TMEM accumulators)
+    forms = {}
+    for fname in ("tc32", "bf16", "fp16"):
+        for path, flag in (("mma_sync", nb.MMA_SYNC), ("tcgen05", nb.TCGEN05)):
+            forms[f"{fname}_{path}_ms"] = timed(
+                lambda: nb.nbfd_var_update(code.handle, F, FORMS[fname] | flag, x, b, a, sym, fsyn))
+    out["variable_node_tensor_core_paths"] = forms
     return out
 
 

@@ -74,6 +74,15 @@ extern "C" {
  * launch that keeps each frame on chip for all of its iterations; both paths give bit-identical
  * outputs. The paper has no counterpart (it is a choice of schedule, not of arithmetic). */
 #define NBFD_UNFUSED 0x400
+/* Path flags for the tensor-core forms (NBFD_FORM_BF16_HGEMM, _FP16_HGEMM, _FP32_TC): the
+ * Hadamard products as tcgen05 MMAs (operands staged in shared memory, FP32 accumulators in tensor
+ * memory, 8 variables' 16 x 16 blocks stacked into M = 128; NBFD_TCGEN05) or as warp-level
+ * mma.sync m16n8k16 (NBFD_MMA_SYNC). Same operand precision, FP32 accumulation either way.
+ * Without a flag each form takes the path measured faster on GB300: tcgen05 for
+ * NBFD_FORM_FP32_TC (three operand parts per product), mma.sync for the BF16 / FP16 forms. Both
+ * flags, or either with another form: NBFD_ENOTSUP. The paper has no counterpart. */
+#define NBFD_TCGEN05 0x800
+#define NBFD_MMA_SYNC 0x1000
 
 typedef struct nbfd_code nbfd_code; /* opaque, library-owned, immutable after creation */
 

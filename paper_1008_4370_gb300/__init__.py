@@ -19,7 +19,7 @@ __all__ = [
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
-    "STORE_F16", "UNFUSED", "KERNEL_FUSED", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
+    "STORE_F16", "UNFUSED", "TCGEN05", "MMA_SYNC", "KERNEL_FUSED", "nbfd_init_messages_f16", "nbfd_check_update_f16", "nbfd_diag_wait_expiry",
     "nbfd_diag_preset_status", "nbfd_diag_fp32_rate", "nbfd_logsp_init", "nbfd_logsp_check_update",
     "nbfd_logsp_var_update",
     "nbfd_last_decode_stats",
@@ -203,6 +203,8 @@ def nbfd_decode(handle, n_frames, llr, max_iter, form, symbols, syndrome_ok, ite
 BATCH_AUTOTUNE = 1
 STORE_F16 = 0x200  # form flag: messages stored as IEEE half (FWHT form, m = 8)
 UNFUSED = 0x400  # form flag: per-iteration kernels even where the fused GF(16) kernel applies
+TCGEN05 = 0x800  # form flag: tensor-core forms on tcgen05 (TMEM accumulators)
+MMA_SYNC = 0x1000  # form flag: tensor-core forms on warp-level mma.sync
 
 
 def nbfd_last_decode_stats():

@@ -23,7 +23,7 @@ LIB = os.path.join(OUT_DIR, "libnbfd.so")
 
 SOURCES = ["code.cpp", "kernels.cu", "kernels_check.cu", "kernels_var_fwht.cu", "kernels_var_fwht8x2.cu", "kernels_var_fwht6x8.cu",
            "kernels_var_fwht4.cu", "kernels_fused_small.cu", "kernels_logsp.cu",
-           "kernels_var_tc.cu",
+           "kernels_var_tc.cu", "kernels_var_tc5.cu",
            "decode.cu", "decode_noalloc.cu", "decode_batch.cu", "server.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I" + INCLUDE, "-I" + CSRC,

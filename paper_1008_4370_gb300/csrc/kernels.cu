@@ -387,9 +387,25 @@ cudaError_t launch_init(const nbfd_code *c, int F, const float *llr, float *lamb
   return cudaGetLastError();
 }
 
+// Tensor-core forms: tcgen05 where asked for, or by default where it measured faster (the FP32
+// form's three operand parts per product; 942 against 989 us per 1024-frame launch, while the
+// single-part BF16 / FP16 forms measured 25-35% slower on tcgen05)
+bool tc_uses_tcgen05(int form) {
+  if (form & NBFD_TCGEN05) return true;
+  if (form & NBFD_MMA_SYNC) return false;
+  return (form & 0xff) == NBFD_FORM_FP32_TC && var_tc5_available();
+}
+
 bool form_supported(int form, int m) {
-  if (form & ~(0xff | NBFD_DECIDE_SYMBOL | NBFD_STORE_F16 | NBFD_UNFUSED)) return false;
+  if (form & ~(0xff | NBFD_DECIDE_SYMBOL | NBFD_STORE_F16 | NBFD_UNFUSED | NBFD_TCGEN05 | NBFD_MMA_SYNC))
+    return false;
   const bool symbol = (form & NBFD_DECIDE_SYMBOL) != 0;
+  if (form & (NBFD_TCGEN05 | NBFD_MMA_SYNC)) {
+    const int b = form & 0xff;
+    if (b != NBFD_FORM_BF16_HGEMM && b != NBFD_FORM_FP16_HGEMM && b != NBFD_FORM_FP32_TC) return false;
+    if ((form & NBFD_TCGEN05) && (form & NBFD_MMA_SYNC)) return false;
+    if ((form & NBFD_TCGEN05) && !var_tc5_available()) return false;
+  }
   if (stores_f16(form)) return (form & 0xff) == NBFD_FORM_FP32_FWHT && m == 8;
   switch (form & 0xff) {
     case NBFD_FORM_FP32_DIRECT:
@@ -416,7 +432,9 @@ cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *l
                                           stores_f16(form))
                      : launch_var_fwht(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   if (base == NBFD_FORM_BF16_HGEMM || base == NBFD_FORM_FP16_HGEMM || base == NBFD_FORM_FP32_TC)
-    return launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
+    return tc_uses_tcgen05(form)
+               ? launch_var_tc5(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune)
+               : launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   const long long total = (long long)fs.n_static * c->N;
   const int per_sm = tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 8;
 #define NBFD_VAR(MB)                                                                       \

@@ -135,6 +135,13 @@ bool form_supported(int form, int m);
 cudaError_t launch_var_tc(const nbfd_code *c, FrameSet fs, int form, const float *llr,
                           const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
                           cudaStream_t s, bool symbol, VarTune tune = {});
+// The same forms on the 5th-generation tensor cores (tcgen05 MMA, accumulators in tensor memory;
+// kernels_var_tc5.cu), on sm_103 devices.
+bool var_tc5_available();
+bool tc_uses_tcgen05(int form);  // the path a tensor-core form runs on (NBFD_TCGEN05 / NBFD_MMA_SYNC)
+cudaError_t launch_var_tc5(const nbfd_code *c, FrameSet fs, int form, const float *llr,
+                           const float *c2v, float *v2c, uint16_t *sym, uint8_t *fsyn,
+                           int32_t *err, cudaStream_t s, bool symbol, VarTune tune = {});
 cudaError_t launch_var_fwht(const nbfd_code *c, FrameSet fs, const float *llr, const float *c2v,
                             float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
                             cudaStream_t s, bool symbol, VarTune tune = {});

@@ -126,7 +126,8 @@ def test_check_update_full_size(dev, name, F):
           f"max lin err {max(s['lin_max'] for s in stats):.2e}, max log err {max(s['log_max'] for s in stats):.2e}")
 
 
-VAR_FORMS = {"gf256_n512_k4": [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT, nb.FORM_FP32_TC],
+VAR_FORMS = {"gf256_n512_k4": [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT, nb.FORM_FP32_TC | nb.MMA_SYNC,
+                               nb.FORM_FP32_TC | nb.TCGEN05],
              "gf64_n1200_k6": [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT]}
 VAR_STATES = [(0.5, 1, True), (1.0, 2, False), (1.5, 1, False), (2.5, 3, False), (2.0, 2, True)]
 

@@ -131,7 +131,8 @@ TC_FORMS = [nb.FORM_BF16_HGEMM, nb.FORM_FP16_HGEMM, nb.FORM_FP32_TC]
 FORM_UNIT = {nb.FORM_FP32_DIRECT: 2.0 ** -24, nb.FORM_FP32_FWHT: 2.0 ** -24, nb.FORM_FP32_TC: 2.0 ** -24,
              nb.FORM_BF16_HGEMM: 2.0 ** -9, nb.FORM_FP16_HGEMM: 2.0 ** -12}
 VAR_CASES = ([(sp, f) for sp in STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6"] for f in FORMS]
-             + [(sp, f) for sp in [(8, 16, 4, 25), (8, 64, 16, 27), "gf256_n512_k4"] for f in TC_FORMS])
+             + [(sp, f | path) for sp in [(8, 16, 4, 25), (8, 64, 16, 27), "gf256_n512_k4"] for f in TC_FORMS
+                for path in (nb.MMA_SYNC, nb.TCGEN05)])
 
 
 def _tolerances(form):
@@ -139,7 +140,7 @@ def _tolerances(form):
     FP32 bounds of helpers.py; the BF16 / FP16 operand forms a bound scaled by their unit
     roundoff u_p: |dP| <= max(16 u_p, 4 u_p kappa), decisions compared where the FP64 margin
     exceeds 0.1."""
-    u = FORM_UNIT[form]
+    u = FORM_UNIT[form & 0xff]
     if u == 2.0 ** -24:
         return None, None, 1e-4, MARGIN
     return 16 * u, 4 * u, 1e9, 0.1
@@ -331,7 +332,7 @@ SPREAD_1024 = [int(x) for x in np.linspace(0, 1023, 16)]
 SPREAD_4096 = [int(x) for x in np.linspace(0, 4095, 16)]
 
 
-@pytest.mark.parametrize("form", FORMS + [nb.FORM_FP32_TC])
+@pytest.mark.parametrize("form", FORMS + [nb.FORM_FP32_TC | nb.MMA_SYNC, nb.FORM_FP32_TC | nb.TCGEN05])
 def test_decode_full_size_gf256_n512(dev, form):
     """The measured configuration: GF(256) (2,4) N=512, 1024 frames at Eb/N0 = 1.5 dB. With at
     most 10 iterations 16 frames spread over the batch (so over the grid's waves and the
@@ -415,7 +416,8 @@ def test_tc_forms_need_m8(dev):
     c = synth.named_code("gf16_n32_k4")
     code = nb.Code(c)
     _, llr = synth.frames(c, 4, 2.0)
-    for form in TC_FORMS:
+    for form in TC_FORMS + [f | nb.TCGEN05 for f in TC_FORMS] + [nb.FORM_FP32_FWHT | nb.TCGEN05,
+                                                                nb.FORM_FP32_FWHT | nb.MMA_SYNC]:
         with pytest.raises(nb.NbfdError) as ei:
             nb.decode(code, _t(llr, dev), 5, form)
         assert ei.value.status == -10

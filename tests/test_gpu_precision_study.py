@@ -25,8 +25,11 @@ from helpers import LOG_FLOOR, U32, decode_pair, encode, oracle_state, to_linear
 pytestmark = pytest.mark.gpu
 
 FORMS = [("fp32_direct", nb.FORM_FP32_DIRECT, U32), ("fp32_fwht", nb.FORM_FP32_FWHT, U32),
-         ("fp32_tc", nb.FORM_FP32_TC, U32), ("bf16_tc", nb.FORM_BF16_HGEMM, 2.0 ** -9),
-         ("fp16_tc", nb.FORM_FP16_HGEMM, 2.0 ** -12)]
+         ("fp32_tc", nb.FORM_FP32_TC | nb.MMA_SYNC, U32), ("bf16_tc", nb.FORM_BF16_HGEMM | nb.MMA_SYNC, 2.0 ** -9),
+         ("fp16_tc", nb.FORM_FP16_HGEMM | nb.MMA_SYNC, 2.0 ** -12)]
+# the tensor-core forms again on tcgen05 (message error only: the same operand precision)
+TC5_FORMS = [("fp32_tc5", nb.FORM_FP32_TC | nb.TCGEN05, U32), ("bf16_tc5", nb.FORM_BF16_HGEMM | nb.TCGEN05, 2.0 ** -9),
+             ("fp16_tc5", nb.FORM_FP16_HGEMM | nb.TCGEN05, 2.0 ** -12)]
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +64,7 @@ def test_message_error_per_form(dev):
         kappa = var_conditions(oc, lam0, c2v_o)[es]
         x = torch.from_numpy(llr).to(dev)
         cin = torch.from_numpy(c2v_in[None]).to(dev)
-        for name, form, u in FORMS:
+        for name, form, u in FORMS + TC5_FORMS:
             out = torch.empty_like(cin)
             nb.nbfd_var_update(code.handle, 1, form, x, cin, out)
             torch.cuda.synchronize()

@@ -123,7 +123,7 @@ def test_binding_constants_equal_the_header():
         "NBFD_STORE_F16": nb.STORE_F16, "NBFD_BATCH_AUTOTUNE": nb.BATCH_AUTOTUNE,
         "NBFD_KERNEL_INIT": nb.KERNEL_INIT, "NBFD_KERNEL_CHECK": nb.KERNEL_CHECK,
         "NBFD_KERNEL_VAR": nb.KERNEL_VAR, "NBFD_KERNEL_SYNDROME": nb.KERNEL_SYNDROME,
-        "NBFD_KERNEL_TAIL": nb.KERNEL_TAIL, "NBFD_KERNEL_FUSED": nb.KERNEL_FUSED, "NBFD_UNFUSED": nb.UNFUSED,
+        "NBFD_KERNEL_TAIL": nb.KERNEL_TAIL, "NBFD_KERNEL_FUSED": nb.KERNEL_FUSED, "NBFD_UNFUSED": nb.UNFUSED, "NBFD_TCGEN05": nb.TCGEN05, "NBFD_MMA_SYNC": nb.MMA_SYNC,
     }
     for name, value in pairs.items():
         assert d[name] == value, name
