@@ -52,6 +52,8 @@ extern "C" {
 #define NBFD_FORM_FP32_FWHT 3   /* fast Walsh-Hadamard butterflies, FP32 */
 #define NBFD_FORM_FP32_TC 4     /* Hadamard transforms on tensor cores, operands split into three
                                    bf16 parts (24 bits) with FP32 accumulate */
+#define NBFD_FORM_FP64_DIRECT 5 /* the direct form with the variable node's sums in FP64 (the
+                                   Section 3.2 convolution step run in FP64; messages stay FP32) */
 /* The tensor-core forms (1, 2, 4) need m = 8 (q = 256 = 16 x 16); other m give NBFD_ENOTSUP. */
 /* Decision flag, OR'ed into a form: the tentative symbol is argmax_x mu_v(x), the symbol-MAP form
  * of Section 3.2 (mu_v = inverse transform of M_v, taken directly from the x-domain product),

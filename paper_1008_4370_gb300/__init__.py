@@ -16,6 +16,7 @@ import numpy as np
 
 __all__ = [
     "NbfdError", "lib", "FORM_FP32_DIRECT", "FORM_BF16_HGEMM", "FORM_FP16_HGEMM", "FORM_FP32_FWHT", "FORM_FP32_TC",
+    "FORM_FP64_DIRECT",
     "nbfd_code_create", "nbfd_code_destroy", "nbfd_code_info", "nbfd_code_edge_order",
     "nbfd_code_index_map", "nbfd_field_index_map", "nbfd_decode_workspace_size", "nbfd_decode", "nbfd_decode_noalloc", "nbfd_init_messages",
     "nbfd_decode_batch_workspace_size", "nbfd_decode_batch", "nbfd_autotune", "nbfd_autotune_result", "BATCH_AUTOTUNE", "decode_batch",
@@ -34,8 +35,9 @@ FORM_BF16_HGEMM = 1
 FORM_FP16_HGEMM = 2
 FORM_FP32_FWHT = 3
 FORM_FP32_TC = 4
+FORM_FP64_DIRECT = 5  # the direct form with the variable node's sums in FP64
 DECIDE_SYMBOL = 0x100  # OR into a form: symbol-MAP tentative decisions
-SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT, FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)
+SUPPORTED_FORMS = (FORM_FP32_DIRECT, FORM_FP32_FWHT, FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC, FORM_FP64_DIRECT)
 TC_FORMS = (FORM_BF16_HGEMM, FORM_FP16_HGEMM, FORM_FP32_TC)  # need m = 8
 KERNEL_INIT, KERNEL_CHECK, KERNEL_VAR, KERNEL_SYNDROME, KERNEL_TAIL, KERNEL_FUSED = 0, 1, 2, 3, 4, 5
 NOALLOC_SCRATCH_BYTES = 64 << 20

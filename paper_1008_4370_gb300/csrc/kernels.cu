@@ -130,8 +130,33 @@ __global__ void __launch_bounds__(256)
 // accumulated as R x R XOR outer products of 16-byte shared-memory blocks, so each step does
 // 2R^2 FMAs for 3R loads. M_v = U1 (*) C1 is then evaluated only at the 3m points the bit and
 // syndrome read-out needs.
-template <int MB>
-__global__ void __launch_bounds__(256)
+// A = float: the plain FP32 form. A = double (NBFD_FORM_FP64_DIRECT): the same step with the
+// check messages decoded, the channel transform taken in closed form (P0(z) = prod over the bits
+// of z of tanh(L_i / 2)), the q^2-term sums, the normalisation and the read-out all in FP64; only
+// the stored messages are FP32.
+template <typename A>
+__device__ __forceinline__ float gamma_encode_t(A r) {
+  if constexpr (sizeof(A) == 8) {
+    const double a = fabs(r);
+    const float mag = a >= 1.0 ? 0.0f : static_cast<float>(-log(a));
+    const uint32_t sg = (a > 0.0) ? ((__double2hiint(r) < 0) ? 0x80000000u : 0u) : 0u;
+    return __uint_as_float(__float_as_uint(mag) | sg);
+  } else {
+    return gamma_encode(r);
+  }
+}
+template <typename A>
+__device__ __forceinline__ A gamma_decode_t(float g) {
+  if constexpr (sizeof(A) == 8) {
+    const double e = exp(-static_cast<double>(fabsf(g)));
+    return signbit(g) ? -e : e;
+  } else {
+    return gamma_decode(g);
+  }
+}
+
+template <int MB, typename A>
+__global__ void __launch_bounds__(sizeof(A) == 8 ? 128 : 256)
     k_var_direct(const float *__restrict__ llr, const float *__restrict__ c2v,
                  float *__restrict__ v2c, uint16_t *__restrict__ sym,
                  uint8_t *__restrict__ fsyn, const int32_t *__restrict__ var_edges,
@@ -143,32 +168,50 @@ __global__ void __launch_bounds__(256)
   constexpr int TPV = Q / R;
   constexpr int VPW = 32 / TPV;
   constexpr int LOG_R = R == 8 ? 3 : (R == 4 ? 2 : 1);
-  __shared__ __align__(16) float sm[8][3][VPW * Q];
+  constexpr int W = sizeof(A) == 8 ? 4 : 8;  // warps per block (FP64: the same shared bytes)
+  __shared__ __align__(16) A sm[W][3][VPW * Q];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / TPV, t = lane % TPV;
-  float *sa_w = sm[wib][0];
-  float *sa = sm[wib][0] + g * Q;
-  float *sc1 = sm[wib][1] + g * Q;
-  float *sc2 = sm[wib][2] + g * Q;
+  A *sa_w = sm[wib][0];
+  A *sa = sm[wib][0] + g * Q;
+  A *sc1 = sm[wib][1] + g * Q;
+  A *sc2 = sm[wib][2] + g * Q;
   const long long total = (long long)frame_count(fs) * N;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = gw * VPW; base < total; base += nw * VPW) {
     // channel message P0 (linear, P0(0) = 1) of the warp's VPW variables
+    if constexpr (sizeof(A) == 8) {
+      for (int k = lane; k < VPW * Q; k += 32) {
+        const int gi = k / Q, z = k % Q;
+        long long item = base + gi;
+        if (item >= total) item = total - 1;
+        const long long slot = item / N;
+        const int v = static_cast<int>(item - slot * N);
+        const int f = frame_at(fs, slot);
+        const float *L = llr + ((size_t)f * N + v) * MB;
+        double p = 1.0;
 #pragma unroll
-    for (int r = 0; r < VPW / CL::VPW; ++r) {
-      const int gi = r * CL::VPW + lane / CL::LPV;
-      long long item = base + gi;
-      if (item >= total) item = total - 1;
-      const long long slot = item / N;
-      const int v = static_cast<int>(item - slot * N);
-      const int f = frame_at(fs, slot);
-      float P[CL::VPT];
-      channel_fourier<MB>(llr + ((size_t)f * N + v) * MB, lane % CL::LPV, P);
-      const float p0 = __shfl_sync(kFull, P[0], (lane / CL::LPV) * CL::LPV);
+        for (int i = 0; i < MB; ++i)
+          if ((z >> i) & 1) p *= tanh(0.5 * static_cast<double>(__ldg(L + i)));
+        sa_w[k] = p;
+      }
+    } else {
 #pragma unroll
-      for (int j = 0; j < CL::VPT; ++j)
-        sa_w[gi * Q + (lane % CL::LPV) * CL::VPT + j] = P[j] / p0;
+      for (int r = 0; r < VPW / CL::VPW; ++r) {
+        const int gi = r * CL::VPW + lane / CL::LPV;
+        long long item = base + gi;
+        if (item >= total) item = total - 1;
+        const long long slot = item / N;
+        const int v = static_cast<int>(item - slot * N);
+        const int f = frame_at(fs, slot);
+        float P[CL::VPT];
+        channel_fourier<MB>(llr + ((size_t)f * N + v) * MB, lane % CL::LPV, P);
+        const float p0 = __shfl_sync(kFull, P[0], (lane / CL::LPV) * CL::LPV);
+#pragma unroll
+        for (int j = 0; j < CL::VPT; ++j)
+          sa_w[gi * Q + (lane % CL::LPV) * CL::VPT + j] = P[j] / p0;
+      }
     }
     const long long item = base + g;
     const bool valid = item < total;
@@ -181,41 +224,58 @@ __global__ void __launch_bounds__(256)
       float x1[R], x2[R];
       load_vec_global<R>(x1, c2v + ((size_t)f * E + e1) * Q + t * R);
       load_vec_global<R>(x2, c2v + ((size_t)f * E + e2) * Q + t * R);
+      if constexpr (sizeof(A) == 8) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        x1[j] = gamma_decode(x1[j]);
-        x2[j] = gamma_decode(x2[j]);
+        for (int j = 0; j < R; ++j) {
+          sc1[t * R + j] = gamma_decode_t<A>(x1[j]);
+          sc2[t * R + j] = gamma_decode_t<A>(x2[j]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          x1[j] = gamma_decode(x1[j]);
+          x2[j] = gamma_decode(x2[j]);
+        }
+        store_vec<R>(sc1 + t * R, x1);
+        store_vec<R>(sc2 + t * R, x2);
       }
-      store_vec<R>(sc1 + t * R, x1);
-      store_vec<R>(sc2 + t * R, x2);
     }
     __syncwarp();
-    float u1[R], u2[R];
+    A u1[R], u2[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) u1[j] = u2[j] = 0.0f;
+    for (int j = 0; j < R; ++j) u1[j] = u2[j] = A(0);
 #pragma unroll 4
     for (int b = 0; b < TPV; ++b) {
-      float av[R], c1v[R], c2v_[R];
-      load_vec<R>(av, sa + b * R);
-      load_vec<R>(c1v, sc1 + (t ^ b) * R);
-      load_vec<R>(c2v_, sc2 + (t ^ b) * R);
+      A av[R], c1v[R], c2v_[R];
+      if constexpr (sizeof(A) == 8) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          av[i] = sa[b * R + i];
+          c1v[i] = sc1[(t ^ b) * R + i];
+          c2v_[i] = sc2[(t ^ b) * R + i];
+        }
+      } else {
+        load_vec<R>(av, sa + b * R);
+        load_vec<R>(c1v, sc1 + (t ^ b) * R);
+        load_vec<R>(c2v_, sc2 + (t ^ b) * R);
+      }
 #pragma unroll
       for (int i = 0; i < R; ++i) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          u1[j] = fmaf(av[i], c2v_[i ^ j], u1[j]);
-          u2[j] = fmaf(av[i], c1v[i ^ j], u2[j]);
+          u1[j] = fma(av[i], c2v_[i ^ j], u1[j]);  // fmaf for A = float
+          u2[j] = fma(av[i], c1v[i ^ j], u2[j]);
         }
       }
     }
-    const float n1 = __shfl_sync(kFull, u1[0], g * TPV);
-    const float n2 = __shfl_sync(kFull, u2[0], g * TPV);
+    const A n1 = __shfl_sync(kFull, u1[0], g * TPV);
+    const A n2 = __shfl_sync(kFull, u2[0], g * TPV);
     if (valid) {
       float o1[R], o2[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        o1[j] = gamma_encode(u1[j] / n1);
-        o2[j] = gamma_encode(u2[j] / n2);
+        o1[j] = gamma_encode_t<A>(u1[j] / n1);
+        o2[j] = gamma_encode_t<A>(u2[j] / n2);
       }
       store_vec<R>(v2c + ((size_t)f * E + e1) * Q + t * R, o1);  // excludes check of e1
       store_vec<R>(v2c + ((size_t)f * E + e2) * Q + t * R, o2);  // excludes check of e2
@@ -224,20 +284,20 @@ __global__ void __launch_bounds__(256)
     // H_e2 alpha^{i-1}. Lane t holds U1 on its block; C1 is read from shared memory.
     const int h1 = __ldg(edge_h + e1), h2 = __ldg(edge_h + e2);
     uint32_t bits = 0, w1 = 0, w2 = 0;
-    const uint32_t neg1 = n1 < 0.0f ? 1u : 0u;
+    const uint32_t neg1 = n1 < A(0) ? 1u : 0u;
 #pragma unroll 1
     for (int i = 0; i < MB; ++i) {
 #pragma unroll
       for (int kind = 0; kind < 3; ++kind) {
         const int zp = kind == 0 ? (1 << i) : __ldg(perm + (kind == 1 ? h1 : h2) * Q + (1 << i));
         const int zb = zp >> LOG_R, zl = zp & (R - 1);
-        const float *cb = sc1 + (t ^ zb) * R;
-        float part = 0.0f;
+        const A *cb = sc1 + (t ^ zb) * R;
+        A part = A(0);
 #pragma unroll
-        for (int j = 0; j < R; ++j) part = fmaf(u1[j], cb[j ^ zl], part);
+        for (int j = 0; j < R; ++j) part = fma(u1[j], cb[j ^ zl], part);
 #pragma unroll
         for (int o = TPV / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-        const uint32_t bit = (part < 0.0f ? 1u : 0u) ^ neg1;
+        const uint32_t bit = (part < A(0) ? 1u : 0u) ^ neg1;
         if (kind == 0) bits |= bit << i;
         else if (kind == 1) w1 |= bit << i;
         else w2 |= bit << i;
@@ -409,6 +469,7 @@ bool form_supported(int form, int m) {
   if (stores_f16(form)) return (form & 0xff) == NBFD_FORM_FP32_FWHT && m == 8;
   switch (form & 0xff) {
     case NBFD_FORM_FP32_DIRECT:
+    case NBFD_FORM_FP64_DIRECT:
       return !symbol;  // its M_v is evaluated only at the 3m read-out points
     case NBFD_FORM_FP32_FWHT:
       return true;
@@ -437,12 +498,21 @@ cudaError_t launch_var(const nbfd_code *c, FrameSet fs, int form, const float *l
                : launch_var_tc(c, fs, base, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune);
   const long long total = (long long)fs.n_static * c->N;
   const int per_sm = tune.blocks_per_sm > 0 ? tune.blocks_per_sm : 8;
+  const bool fp64 = base == NBFD_FORM_FP64_DIRECT;
 #define NBFD_VAR(MB)                                                                       \
   {                                                                                        \
     constexpr int Q = 1 << MB, R = Q < 8 ? Q : 8, VPW = 32 / (Q / R);                      \
-    const int grid = grid_for((total + 8 * VPW - 1) / (8 * VPW), per_sm);                  \
-    k_var_direct<MB><<<grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn, c->d_var_edges,        \
-                                          c->d_edge_h, c->d_perm, c->N, c->E, fs);         \
+    if (fp64) {                                                                            \
+      const int grid = grid_for((total + 4 * VPW - 1) / (4 * VPW), 2 * per_sm);            \
+      k_var_direct<MB, double><<<grid, 128, 0, s>>>(llr, c2v, v2c, sym, fsyn,              \
+                                                    c->d_var_edges, c->d_edge_h, c->d_perm, \
+                                                    c->N, c->E, fs);                       \
+    } else {                                                                               \
+      const int grid = grid_for((total + 8 * VPW - 1) / (8 * VPW), per_sm);                \
+      k_var_direct<MB, float><<<grid, 256, 0, s>>>(llr, c2v, v2c, sym, fsyn,               \
+                                                   c->d_var_edges, c->d_edge_h, c->d_perm, \
+                                                   c->N, c->E, fs);                        \
+    }                                                                                      \
   }
   NBFD_DISPATCH_M(c->m, NBFD_VAR)
 #undef NBFD_VAR

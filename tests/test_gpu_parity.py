@@ -129,8 +129,10 @@ FORMS = [nb.FORM_FP32_DIRECT, nb.FORM_FP32_FWHT]
 TC_FORMS = [nb.FORM_BF16_HGEMM, nb.FORM_FP16_HGEMM, nb.FORM_FP32_TC]
 # unit roundoff of the operands each form rounds to (FP32 forms: 2^-24)
 FORM_UNIT = {nb.FORM_FP32_DIRECT: 2.0 ** -24, nb.FORM_FP32_FWHT: 2.0 ** -24, nb.FORM_FP32_TC: 2.0 ** -24,
+             nb.FORM_FP64_DIRECT: 2.0 ** -24,
              nb.FORM_BF16_HGEMM: 2.0 ** -9, nb.FORM_FP16_HGEMM: 2.0 ** -12}
 VAR_CASES = ([(sp, f) for sp in STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6"] for f in FORMS]
+             + [(sp, nb.FORM_FP64_DIRECT) for sp in ["gf16_n32_k4", (6, 24, 6, 23), (8, 16, 4, 25), "gf256_n512_k4"]]
              + [(sp, f | path) for sp in [(8, 16, 4, 25), (8, 64, 16, 27), "gf256_n512_k4"] for f in TC_FORMS
                 for path in (nb.MMA_SYNC, nb.TCGEN05)])
 

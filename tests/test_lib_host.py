@@ -119,7 +119,8 @@ def test_binding_constants_equal_the_header():
     pairs = {
         "NBFD_FORM_FP32_DIRECT": nb.FORM_FP32_DIRECT, "NBFD_FORM_BF16_HGEMM": nb.FORM_BF16_HGEMM,
         "NBFD_FORM_FP16_HGEMM": nb.FORM_FP16_HGEMM, "NBFD_FORM_FP32_FWHT": nb.FORM_FP32_FWHT,
-        "NBFD_FORM_FP32_TC": nb.FORM_FP32_TC, "NBFD_DECIDE_SYMBOL": nb.DECIDE_SYMBOL,
+        "NBFD_FORM_FP32_TC": nb.FORM_FP32_TC, "NBFD_FORM_FP64_DIRECT": nb.FORM_FP64_DIRECT,
+        "NBFD_DECIDE_SYMBOL": nb.DECIDE_SYMBOL,
         "NBFD_STORE_F16": nb.STORE_F16, "NBFD_BATCH_AUTOTUNE": nb.BATCH_AUTOTUNE,
         "NBFD_KERNEL_INIT": nb.KERNEL_INIT, "NBFD_KERNEL_CHECK": nb.KERNEL_CHECK,
         "NBFD_KERNEL_VAR": nb.KERNEL_VAR, "NBFD_KERNEL_SYNDROME": nb.KERNEL_SYNDROME,
