@@ -238,6 +238,7 @@ cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, floa
 #define NBFD_CHK_M(MB)                     \
   {                                        \
     if (k <= 4) NBFD_CHK(MB, 4)            \
+    else if (k <= 6) NBFD_CHK(MB, 6)       \
     else if (k <= 8) NBFD_CHK(MB, 8)       \
     else if (k <= 16) NBFD_CHK(MB, 16)     \
     else NBFD_CHK(MB, 32)                  \

@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
       float4 *t4 = reinterpret_cast<float4 *>(wm.tile);
       for (int i = lane; i < k * (kQ / 4); i += 32) t4[i] = __ldcg(src + i);
       __syncwarp();
-      check_lane_inplace<kQ, 8, KMAX, float>(wm.tile, c, k, 8 * lane, edge_h, perm);
+      check_lane_inplace<kQ, 8, KMAX, float, 1>(wm.tile, c, k, 8 * lane, edge_h, perm);
       __syncwarp();
       float4 *dst = reinterpret_cast<float4 *>(c2v + (fE + (size_t)c * k) * kQ);
       for (int i = lane; i < k * (kQ / 4); i += 32) dst[i] = t4[i];
