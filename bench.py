@@ -479,7 +479,8 @@ def uneven_leg(nb, torch, dev, form, steps, max_iter):
     return {"codes": [n for n, _ in UNEVEN], "frames": ns, "info_bits_per_step": bits,
             "value": res["batch"]["mbit_s"], "unit": "Mbit/s", "ms_per_step": res["batch"]["ms_per_step"],
             "per_code_calls": res["per_code"], "steps": steps, "decoded_frac": oks, "mean_iterations": its,
-            "tuned_shapes": [{"check_warps": t[0], "check_stages": t[1], "check_blocks_per_sm": t[2],
+            "tuned_shapes": [{"check_warps": abs(t[0]), "check_team": t[0] < 0, "check_stages": t[1],
+                              "check_blocks_per_sm": t[2],
                               "var_blocks_per_sm": t[3], "var_warps": t[4]} if t else "fused small-code kernel"
                              for t in tunes],
             "ebn0_db": "per frame U[1.0, 3.5]", "max_iter": max_iter}

@@ -193,7 +193,8 @@ int nbfd_decode_batch(int n_codes, const nbfd_code *const *codes, const int *n_f
 
 /*
  * nbfd_autotune -- time candidate launch shapes of the check kernel (warps per block, bulk-copy
- * pipeline depth, blocks per SM) and of the variable-node kernel (blocks per SM; warps per block
+ * pipeline depth, blocks per SM; for q >= 128 also its team variant) and of the variable-node
+ * kernel (blocks per SM; warps per block
  * for GF(64)) for this code,
  * n_frames and form, on scratch buffers it allocates on `cuda_stream`, and keep the fastest.
  * Later nbfd_decode / nbfd_decode_batch calls with the same device, code shape (N, k, m),
@@ -202,9 +203,11 @@ int nbfd_decode_batch(int n_codes, const nbfd_code *const *codes, const int *n_f
  */
 int nbfd_autotune(const nbfd_code *code, int n_frames, int form, void *cuda_stream);
 
-/* The shape nbfd_autotune chose (NBFD_EINVAL if this shape was never tuned). var_warps: warps per
- * block of the variable-node kernel where it has several block shapes (GF(64): 4, 7 or 15), 0
- * where it has one. Any out pointer may be NULL. */
+/* The shape nbfd_autotune chose (NBFD_EINVAL if this shape was never tuned). check_warps < 0:
+ * the check kernel's team variant, where the -check_warps warps of a block share one pipeline of
+ * whole checks (q >= 128; check_stages is then per block). var_warps: warps per block of the
+ * variable-node kernel where it has several block shapes (GF(64): 4, 7 or 15), 0 where it has
+ * one. Any out pointer may be NULL. */
 int nbfd_autotune_result(const nbfd_code *code, int n_frames, int form, int *check_warps,
                          int *check_stages, int *check_blocks_per_sm, int *var_blocks_per_sm,
                          int *var_warps);

@@ -16,7 +16,9 @@ namespace nbfd {
 // Entries of a lane gathered together: up to 4 for row weights up to 6 (measured on GB300: the
 // GF(64) k = 6 check goes from 0.77 to 0.99 of HBM bandwidth, GF(32) k = 6 from 0.74 to 0.98).
 // From k = 8 on, one entry's k loads already keep the lane busy and the registers of a group cost
-// occupancy (GF(64) k = 8: 0.81 with one entry, 0.75 with two), so entries go one at a time.
+// occupancy (GF(64) k = 8: 0.87 with one entry, 0.75 with two), so entries go one at a time --
+// for k = 8 still gathered before any arithmetic (0.87, against 0.69 with the loads interleaved
+// with the magnitude and sign work as for k > 8, where that form needs fewer registers).
 __host__ __device__ constexpr int check_gather_group(int epl, int kmax) {
   return kmax > 6 ? 1 : (epl < 4 ? epl : 4);
 }
@@ -75,6 +77,8 @@ __device__ __forceinline__ void check_lane_inplace(W *s, int c, int k, int z0,
         pw[e][1] = w.y;
       } else if constexpr (EPL == 4) {
         pw[e][0] = __ldg(reinterpret_cast<const uint32_t *>(row));
+      } else if constexpr (EPL == 2) {
+        pw[e][0] = __ldg(reinterpret_cast<const uint16_t *>(row));
       } else {
         uint32_t w = 0;
 #pragma unroll
@@ -88,7 +92,7 @@ __device__ __forceinline__ void check_lane_inplace(W *s, int c, int k, int z0,
   // store of one entry misses the next entry's loads, and would otherwise serialise the entries.
   // Both branches compute every output with the same operations in the same order.
   constexpr int G = check_gather_group(EPL, KMAX) < MAXG ? check_gather_group(EPL, KMAX) : MAXG;
-  if constexpr (G == 1) {  // one entry at a time
+  if constexpr (G == 1 && (KMAX > 8 || MAXG == 1)) {  // one entry at a time, loads interleaved
 #pragma unroll
     for (int j = 0; j < EPL; ++j) {
       float mag[KMAX];

@@ -100,6 +100,27 @@ int tune_code(const nbfd_code *c, int F, int form, const float *llr, float *v2c,
       }
     }
   }
+  if (c->q >= 128) {  // the team variant: a block's warps share one pipeline of whole checks
+    const long long checks = (long long)F * c->M;
+    for (int stages : {3, 4, 6}) {
+      const size_t smem = 128 + (size_t)stages * c->k * c->q * (stores_f16(form) ? 2 : 4);
+      if (smem > kMaxSmemPerBlock) continue;
+      const int fit = static_cast<int>((228 * 1024) / (smem + 1024));
+      for (int bps : {1, 2, 3, 4, 6, 8, 2 * fit, 4 * fit, 8 * fit}) {
+        const bool over = bps > fit;
+        if (bps > 16 && !over) continue;
+        if ((long long)bps * sms * (over ? 4 : 1) > checks * (over ? 1 : 2) && bps > 1) continue;
+        CheckTune ct{0, stages, bps, 1};
+        const float ms = time_launches(s, 3, [&] {
+          return launch_check(c, fs, v2c, c2v, s, nullptr, {}, ct, stores_f16(form));
+        });
+        if (ms > 0.0f && (best_ms < 0.0f || ms < best_ms)) {
+          best_ms = ms;
+          best.check = ct;
+        }
+      }
+    }
+  }
   if (best_ms < 0.0f) return set_error(NBFD_ECUDA, "autotune: no check-kernel shape ran");
   best_ms = -1.0f;
   const bool x8 = (form & 0xff) == NBFD_FORM_FP32_FWHT && var_fwht6x8_applies(c);
@@ -246,7 +267,7 @@ extern "C" int nbfd_autotune_result(const nbfd_code *c, int F, int form, int *ch
   CheckTune ct;
   VarTune vt;
   if (!tune_lookup(c, F, form, &ct, &vt)) return set_error(NBFD_EINVAL, "shape not tuned");
-  if (check_warps) *check_warps = ct.warps;
+  if (check_warps) *check_warps = ct.team > 0 ? -kCheckTeamWarps : ct.warps;
   if (check_stages) *check_stages = ct.stages;
   if (check_blocks_per_sm) *check_blocks_per_sm = ct.blocks_per_sm;
   if (var_blocks_per_sm) *var_blocks_per_sm = vt.blocks_per_sm;

@@ -195,10 +195,152 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Team variant for tiles of one whole check (q >= 128): the kTeam warps of a block share one
+// S-stage pipeline, so an SM holds a block's S tiles per kTeam warps instead of S per warp. At
+// q = 256 and k = 16 a check is 16 KiB: three stages per warp left 4 warps on an SM, the team
+// variant keeps 16. Thread t works on entries t*EPL .. t*EPL+EPL-1 of the check; thread 0 drives
+// the bulk copies; block barriers separate the in-place work from the write-back.
+constexpr int kTeam = kCheckTeamWarps;
+
+template <int MB, int KMAX, typename W, bool L0>
+__global__ void __launch_bounds__(32 * kTeam, KMAX <= 16 ? 4 : 2)
+    k_check_team(const W *__restrict__ v2c, W *__restrict__ c2v,
+                 const uint8_t *__restrict__ edge_h, const uint8_t *__restrict__ perm, int M, int k,
+                 int E, int S, FrameSet fs, int32_t *err, LoopTick tick,
+                 const int32_t *__restrict__ edge_var, int N) {
+  constexpr int Q = 1 << MB, EPL = Q / (32 * kTeam);
+  static_assert(EPL >= 1 && EPL * 32 * kTeam == Q, "one check per tile");
+  griddep_wait();
+  griddep_release();
+  if (tick.iter && blockIdx.x == 0 && threadIdx.x == 0) {
+    *tick.iter += 1;
+    *tick.zero = 0;
+  }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  const size_t tile = (size_t)k * Q;
+  W *stages = reinterpret_cast<W *>(smem_raw + 128);
+  const int tid = threadIdx.x;
+  const long long total = (long long)n_frames_of(fs) * M;
+  const bool narrow = total < (1ll << 32);
+  const long long gb = blockIdx.x, nb = gridDim.x;
+  const long long my_count = gb < total ? (total - gb + nb - 1) / nb : 0;
+  if (my_count == 0) return;  // block-uniform
+  if (tid == 0) {
+    for (int b = 0; b < S; ++b) mbar_init(&bars[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  long long issued = 0;  // thread 0's count of tiles whose loads it issued
+  auto issue = [&](long long j) {
+    const long long tj = gb + j * nb;
+    const int bj = static_cast<int>(j % S);
+    mbar_expect_tx(&bars[bj], static_cast<uint32_t>(tile * sizeof(W)));
+    if constexpr (L0)
+      stage_copies_l0<W>(fs, tj, 1, total, M, k, N, Q, v2c, edge_var, stages + bj * tile,
+                         &bars[bj]);
+    else
+      stage_copies<true, W>(fs, tj, 1, total, M, k, E, Q, v2c, nullptr, stages + bj * tile,
+                            &bars[bj]);
+  };
+  if (tid == 0)
+    for (; issued < S - 2 && issued < my_count; ++issued) issue(issued);
+  long long i = 0;
+  bool failed = false;
+  for (; i < my_count; ++i) {
+    const int b = static_cast<int>(i % S);
+    const long long item = gb + i * nb;
+    if (tid == 0 && issued < my_count) {
+      bulk_wait_read_all_but_one();  // the buffer of tile i-2 was written back
+      issue(issued);
+      ++issued;
+    }
+    const bool ok = mbar_wait_bounded(&bars[b], static_cast<uint32_t>((i / S) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const int c = static_cast<int>(item - div_m(item, M, narrow) * M);
+    check_lane_inplace<Q, EPL, KMAX, W>(stages + b * tile, c, k, tid * EPL, edge_h, perm);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      stage_copies<false, W>(fs, item, 1, total, M, k, E, Q, nullptr, c2v, stages + b * tile,
+                             nullptr);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) {
+    if (failed) {
+      if (err) atomicExch(err, NBFD_ETIMEDOUT);
+      for (long long j = i; j < issued; ++j)
+        mbar_wait_bounded(&bars[j % S], static_cast<uint32_t>((j / S) & 1));
+    }
+    bulk_wait_read_all();  // the CTA's shared memory must outlive the bulk stores' reads
+  }
+}
+
+// The team variant's launch (q = 128 or 256).
+static cudaError_t launch_check_team(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
+                                     cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune,
+                                     bool f16, const float *lambda0) {
+  const int Q = c->q, k = c->k;
+  const size_t wb = f16 ? 2 : 4;
+  const int S = tune.stages > 0 ? tune.stages : 3;
+  const size_t smem = 128 + (size_t)S * k * Q * wb;
+  if (S < 3 || S > 8 || smem > kMaxSmemPerBlock || (c->m != 7 && c->m != 8))
+    return cudaErrorInvalidValue;
+  const long long total = (long long)fs.n_static * c->M;
+  int fill = static_cast<int>((228 * 1024) / (smem + 1024));
+  fill = fill < 1 ? 1 : (fill > 16 ? 16 : fill);
+  const int per_sm = tune.blocks_per_sm > 0
+                         ? tune.blocks_per_sm
+                         : fill * oversubscribed_waves(total, (long long)sm_count() * fill);
+  long long grid = (long long)sm_count() * per_sm;
+  if (grid > total) grid = total;
+  if (grid < 1) grid = 1;
+#define NBFD_TEAM_T(MB, KM, W, L0)                                                             \
+  {                                                                                             \
+    const cudaError_t ae = ensure_smem((const void *)k_check_team<MB, KM, W, L0>, smem);        \
+    if (ae != cudaSuccess) return ae;                                                           \
+    const cudaError_t le = launch_dependent(                                                    \
+        k_check_team<MB, KM, W, L0>, dim3((int)grid), dim3(32 * kTeam), smem, s,               \
+        reinterpret_cast<const W *>(L0 ? lambda0 : v2c), reinterpret_cast<W *>(c2v),            \
+        c->d_edge_h, c->d_perm, c->M, k, c->E, S, fs, err, tick, c->d_edge_var, c->N);          \
+    if (le != cudaSuccess) return le;                                                           \
+    return cudaGetLastError();                                                                  \
+  }
+#define NBFD_TEAM_K(MB, W, L0)                     \
+  {                                                \
+    if (k <= 4) NBFD_TEAM_T(MB, 4, W, L0)          \
+    else if (k <= 8) NBFD_TEAM_T(MB, 8, W, L0)     \
+    else if (k <= 16) NBFD_TEAM_T(MB, 16, W, L0)   \
+    else NBFD_TEAM_T(MB, 32, W, L0)                \
+  }
+  if (f16) {
+    if (c->m != 8) return cudaErrorNotSupported;
+    NBFD_TEAM_K(8, __half, false)
+  }
+  if (c->m == 8) {
+    if (lambda0) NBFD_TEAM_K(8, float, true)
+    NBFD_TEAM_K(8, float, false)
+  }
+  if (lambda0) NBFD_TEAM_K(7, float, true)
+  NBFD_TEAM_K(7, float, false)
+#undef NBFD_TEAM_K
+#undef NBFD_TEAM_T
+}
+
+// Built-in choice of the team variant: one-check tiles of 8 KiB or more, where per-warp stages
+// would leave an SM few warps.
+static bool team_default(const nbfd_code *c) { return c->q >= 128 && c->k > 8; }
+
 cudaError_t launch_check(const nbfd_code *c, FrameSet fs, const float *v2c, float *c2v,
                          cudaStream_t s, int32_t *err, LoopTick tick, CheckTune tune, bool f16,
                          const float *lambda0) {
   if (lambda0 && f16) return cudaErrorNotSupported;
+  const bool team = tune.team > 0 || (tune.team < 0 && tune.warps == 0 && team_default(c));
+  if (team) return launch_check_team(c, fs, v2c, c2v, s, err, tick, tune, f16, lambda0);
   const int Q = c->q, k = c->k;
   const size_t wb = f16 ? 2 : 4;  // bytes per stored message entry
   const int epl = Q < 8 ? Q : 8;

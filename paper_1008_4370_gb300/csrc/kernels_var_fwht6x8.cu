@@ -191,10 +191,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     for (int q = 0; q < 4; ++q) {
       const float4 a = *reinterpret_cast<const float4 *>(&ws.msg[b][g][4 * l + 16 * q]);
       const float4 d = *reinterpret_cast<const float4 *>(&ws.msg[b][g][kQ6 + 4 * l + 16 * q]);
-      c[4 * q + 0] = make_float2(gamma_decode_ftz(a.x), gamma_decode_ftz(d.x));
-      c[4 * q + 1] = make_float2(gamma_decode_ftz(a.y), gamma_decode_ftz(d.y));
-      c[4 * q + 2] = make_float2(gamma_decode_ftz(a.z), gamma_decode_ftz(d.z));
-      c[4 * q + 3] = make_float2(gamma_decode_ftz(a.w), gamma_decode_ftz(d.w));
+      // packed pairs along the 16-byte loads (aligned register pairs)
+      const float2 ax = gamma_decode2_ftz(a.x, a.y), az = gamma_decode2_ftz(a.z, a.w);
+      const float2 dx = gamma_decode2_ftz(d.x, d.y), dz = gamma_decode2_ftz(d.z, d.w);
+      c[4 * q + 0] = make_float2(ax.x, dx.x);
+      c[4 * q + 1] = make_float2(ax.y, dx.y);
+      c[4 * q + 2] = make_float2(az.x, dz.x);
+      c[4 * q + 3] = make_float2(az.y, dz.y);
     }
     // forward transforms of the pair, P0 -> P1
     stage<0>(c);
@@ -276,8 +279,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float2 sc = __ffma2_rn(c[4 * q + i], r, make_float2(0.0f, 0.0f));  // -0 -> +0
-          o2[i] = gamma_encode_ftz(sc.x);
-          o1[i] = gamma_encode_ftz(sc.y);
+          const float2 o = gamma_encode2_ftz(sc);
+          o2[i] = o.x;
+          o1[i] = o.y;
         }
         if (q == 0 && l == 0) {
           o2[0] = 0.0f;  // Gamma(1)

@@ -178,10 +178,13 @@ __device__ __forceinline__ void x2_unit(const W *msg0, const W *msg1, const floa
   for (int g = 0; g < 4; ++g) {
     const float4 a = load4(&msg0[4 * l + 64 * g]);
     const float4 d = load4(&msg1[4 * l + 64 * g]);
-    c[4 * g + 0] = make_float2(gamma_decode_ftz(a.x), gamma_decode_ftz(d.x));
-    c[4 * g + 1] = make_float2(gamma_decode_ftz(a.y), gamma_decode_ftz(d.y));
-    c[4 * g + 2] = make_float2(gamma_decode_ftz(a.z), gamma_decode_ftz(d.z));
-    c[4 * g + 3] = make_float2(gamma_decode_ftz(a.w), gamma_decode_ftz(d.w));
+    // packed pairs along the 16-byte loads (aligned register pairs)
+    const float2 ax = gamma_decode2_ftz(a.x, a.y), az = gamma_decode2_ftz(a.z, a.w);
+    const float2 dx = gamma_decode2_ftz(d.x, d.y), dz = gamma_decode2_ftz(d.z, d.w);
+    c[4 * g + 0] = make_float2(ax.x, dx.x);
+    c[4 * g + 1] = make_float2(ax.y, dx.y);
+    c[4 * g + 2] = make_float2(az.x, dz.x);
+    c[4 * g + 3] = make_float2(az.y, dz.y);
   }
   // forward transforms of the pair (q x-domain check messages), P0 -> P1
   stages4(c);
@@ -248,8 +251,9 @@ __device__ __forceinline__ void x2_unit(const W *msg0, const W *msg1, const floa
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float2 sc = __ffma2_rn(c[4 * g + i], r, make_float2(0.0f, 0.0f));  // -0 -> +0
-        o2[i] = gamma_encode_ftz(sc.x);
-        o1[i] = gamma_encode_ftz(sc.y);
+        const float2 o = gamma_encode2_ftz(sc);
+        o2[i] = o.x;
+        o1[i] = o.y;
       }
       if (g == 0 && l == 0) {
         o2[0] = 0.0f;  // Gamma(1)

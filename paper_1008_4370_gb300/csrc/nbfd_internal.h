@@ -46,14 +46,17 @@ struct LoopTick {
 // Launch shapes picked by the autotuner (0 = the built-in default).
 struct CheckTune {
   int warps = 0;          // warps per block, 1..8
-  int stages = 0;         // bulk-copy pipeline depth per warp, 3..8
+  int stages = 0;         // bulk-copy pipeline depth per warp (per block with `team`), 3..8
   int blocks_per_sm = 0;  // grid cap in blocks per SM
+  int team = -1;          // 1: the block's warps share one pipeline of whole checks (q >= 128),
+                          // 0: one pipeline per warp, -1: the built-in choice
 };
 struct VarTune {
   int blocks_per_sm = 0;  // grid cap in blocks per SM
   int warps = 0;          // warps per block where the kernel has several shapes (GF(64): 4, 7, 15)
 };
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;
+constexpr int kCheckTeamWarps = 4;  // warps of a block of the check kernel's team variant
 // Waves of resident blocks for a grid-stride kernel with `work` items over `warps_per_wave`
 // warps: one wave leaves the warps' finishing times uneven (memory bandwidth is not shared
 // evenly), so the grid is oversubscribed -- up to 8 waves, the block scheduler then evening out

@@ -1,6 +1,7 @@
 """Full-size teacher-forced parity of the check-node and variable-node kernels: GF(256) (2,4)
 N=512 at 1024 frames and GF(64) (2,6) N=1200 at 4096 frames, the batch sizes the configurations
-name, through the step-level C ABI calls (the kernels, grids and pipelines nbfd_decode launches).
+name, and for the check node also GF(256) (2,16) N=2048 at 256 frames, through the step-level C
+ABI calls (the kernels, grids and pipelines nbfd_decode launches).
 
 Inputs are distinct per frame and still checkable everywhere. A handful of oracle message states
 (G "virtual frames": several Eb/N0, iterations and saturated / zero-information LLRs) form a pool;
@@ -78,7 +79,11 @@ def _mismatch(o, g, unit_of_slot=None):
     return (rep != o).reshape(F, o.shape[1], -1).any(-1)
 
 
-@pytest.mark.parametrize("name,F", FULL)
+# the uneven batch's GF(256) (2,16) N=2048 group (256 frames): the check kernel's team variant
+FULL_CHECK = FULL + [("gf256_n2048_k16", 256)]
+
+
+@pytest.mark.parametrize("name,F", FULL_CHECK)
 def test_check_update_full_size(dev, name, F):
     c = synth.named_code(name)
     oc = OracleCode.from_dict(c)

@@ -102,7 +102,10 @@ def test_init_parity(dev, spec):
         assert np.all(g_lam0[f][:, 0] == 0.0) and not np.any(np.signbit(g_lam0[f][:, 0]))
 
 
-@pytest.mark.parametrize("spec", STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6"])
+# row weights above 8 at q >= 128 run the check kernel's team variant (a block shares one
+# pipeline of whole checks): GF(128) k = 10 and GF(256) k = 20 beside (8, 64, 16, 27) above
+@pytest.mark.parametrize("spec", STEP_CODES + ["gf256_n512_k4", "gf64_n1200_k6", (7, 40, 10, 29),
+                                  (8, 60, 20, 30)])
 def test_check_parity(dev, spec):
     c = _code(spec)
     oc = OracleCode.from_dict(c)
