@@ -113,15 +113,20 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   const long long step_s = (8 * nw) / N;
   const int step_v = static_cast<int>(8 * nw - step_s * N);
   int pf_f = 0, pf_v = 0;
-  auto load_next = [&]() {  // lane 0
-    pf_f = fs.list ? __ldg(fs.list + cur_slot) : static_cast<int>(cur_slot);
-    pf_v = cur_v;
-    cur_slot += step_s;
-    cur_v += step_v;
-    if (cur_v >= N) {
-      cur_v -= N;
-      ++cur_slot;
+  int2 pf_e = make_int2(0, 0);  // lanes 0..7: the edges of variable pf_v + lane, loaded a unit early
+  auto load_next = [&]() {  // lane 0 steps, then lanes 0..7 start loading the edges
+    if (lane == 0) {
+      pf_f = fs.list ? __ldg(fs.list + cur_slot) : static_cast<int>(cur_slot);
+      pf_v = cur_v;
+      cur_slot += step_s;
+      cur_v += step_v;
+      if (cur_v >= N) {
+        cur_v -= N;
+        ++cur_slot;
+      }
     }
+    const int v = __shfl_sync(kFull, pf_v, 0);
+    if (lane < 8) pf_e = __ldg(reinterpret_cast<const int2 *>(var_edges) + v + lane);
   };
   // all lanes: lane 0 arms the barrier, lanes 0..7 issue their variable's two message copies,
   // lane 8 the LLR block (one SIMT instruction each)
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     if (lane == 0) mbar_expect_tx(&ws.bar[st], 8u * 2u * kQ6 * 4u + 8u * 6u * 4u);
     __syncwarp();
     if (lane < 8) {
-      const int2 e = __ldg(reinterpret_cast<const int2 *>(var_edges) + v0 + lane);
+      const int2 e = pf_e;
       ws.idx[st][lane] = make_int4(f, v0 + lane, e.x, e.y);
       bulk_load(&ws.msg[st][lane][0], c2v + ((size_t)f * E + e.x) * kQ6, kQ6 * 4u, &ws.bar[st]);
       bulk_load(&ws.msg[st][lane][kQ6], c2v + ((size_t)f * E + e.y) * kQ6, kQ6 * 4u, &ws.bar[st]);
@@ -144,10 +149,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   }
   __syncwarp();
   for (int k = 0; k < S - 1 && k < n_units; ++k) {
-    if (lane == 0) load_next();
+    load_next();
     issue(k, __shfl_sync(kFull, pf_f, 0), __shfl_sync(kFull, pf_v, 0));
   }
-  if (lane == 0 && S - 1 < n_units) load_next();
+  if (S - 1 < n_units) load_next();
   __syncwarp();
   // per-lane transpose offsets: P0 lanes hold x2, x3; P1 lanes hold x0, x1
   const int o0 = g * kVar + ((l & 1) ? w6(2) : 0) + ((l & 2) ? w6(3) : 0);
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
       __syncwarp();
       issue(static_cast<int>((t + S - 1) % S), __shfl_sync(kFull, pf_f, 0),
             __shfl_sync(kFull, pf_v, 0));
-      if (lane == 0 && t + S < n_units) load_next();
+      if (t + S < n_units) load_next();
     }
     const bool ok = mbar_wait_bounded(&ws.bar[b], static_cast<uint32_t>((t / S) & 1));
     if (__any_sync(kFull, !ok)) {
@@ -174,6 +179,20 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     }
     const int4 ix = ws.idx[b][g];
     const int f = ix.x, v = ix.y, e1 = ix.z, e2 = ix.w;
+    // TENTATIVE read-out points of this lane, loaded now and used at the end: 18 per variable,
+    // 4 per round (point p = 4 round + l): p < 6 alpha^p, p < 12 H_e1 alpha^(p-6), p < 18 H_e2
+    // alpha^(p-12)
+    int zr[5];
+    if constexpr (!SYMBOL) {
+#pragma unroll
+      for (int round = 0; round < 5; ++round) {
+        const int p = 4 * round + l;
+        const int kind = p / 6, i = p - 6 * kind;
+        zr[round] = p >= 18 ? 0
+                    : kind == 0 ? (1 << i)
+                                : __ldg(edge_z + (size_t)(kind == 1 ? e1 : e2) * 8 + i);
+      }
+    }
     // channel bit probabilities: lanes 0, 1 of a group compute bits l and l + 4, lanes 2, 3 bit l
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -328,18 +347,11 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
       *reinterpret_cast<float4 *>(m_nat + 4 * l + 32) = make_float4(mp[0].y, mp[1].y, mp[2].y, mp[3].y);
       *reinterpret_cast<float4 *>(m_nat + 4 * l + 48) = make_float4(mp[4].y, mp[5].y, mp[6].y, mp[7].y);
       __syncwarp();
-      // TENTATIVE: 18 read-out points per variable, 4 per round (point p = 4 round + l): p < 6
-      // alpha^p, p < 12 H_e1 alpha^(p-6), p < 18 H_e2 alpha^(p-12)
+      // TENTATIVE: the signs of M at the read-out points zr, gathered with ballots
       uint32_t word = 0;
 #pragma unroll
       for (int round = 0; round < 5; ++round) {
-        const int p = 4 * round + l;
-        bool neg = false;
-        if (p < 18) {
-          const int kind = p / 6, i = p - 6 * kind;
-          const int z = kind == 0 ? (1 << i) : __ldg(edge_z + (size_t)(kind == 1 ? e1 : e2) * 8 + i);
-          neg = m_nat[z] < 0.0f;
-        }
+        const bool neg = 4 * round + l < 18 && m_nat[zr[round]] < 0.0f;
         const uint32_t bal = __ballot_sync(kFull, neg);
         word |= ((bal >> (4 * g)) & 0xfu) << (4 * round);
       }
