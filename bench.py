@@ -41,17 +41,18 @@ FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 # code), with the sources the kernel was built from and the first 16 hex digits of the SHA-256 of
 # their concatenation at capture time. A changed source voids the figure (reported as null).
 # Capture: ncu --set full --clock-control none -k regex:<kernel> -s 2 -c 1 python bench.py
-#          --frames 256 --steps 1 --warmup 1 --no-cpu-baseline --serve-requests 0 --plain-steps 0
-#          --batches 1 --form fwht --store16-steps 0 --uneven-steps 0
+#          --frames 256 --steps 1 --warmup 1 --batches 1 --form fwht --no-cpu-baseline
+#          --serve-requests 0 --plain-steps 0 --store16-steps 0 --uneven-steps 0 --gf64-steps 0
+#          --fused-steps 0 --table1-reps 0 --serve-mix-loads
 MEASURED_TRAFFIC = {
     ("var", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (272704768 + 218983168) / 256,
+        "bytes_per_frame": (272749824 + 219516160) / 256,
         "sources": ["kernels_var_fwht8x2.cu", "check_math.cuh", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "3ce20a16890dd27b"},
+        "sha256_16": "642f4ccd31809670"},
     ("check", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (268668928 + 213665792) / 256,
+        "bytes_per_frame": (268656128 + 216033024) / 256,
         "sources": ["kernels_check.cu", "check_math.cuh", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "29572d9ec2ab1c44"},
+        "sha256_16": "1fbe24cd311b7b75"},
 }
 
 
