@@ -59,13 +59,18 @@ __device__ __forceinline__ void check_entry_store(W *s, int k, const float (&x)[
   }
 }
 
-// MAXG caps the gather group (1 for a caller whose register budget has no room for it).
-template <int Q, int EPL, int KMAX, typename W, int MAXG = EPL>
-__device__ __forceinline__ void check_lane_inplace(W *s, int c, int k, int z0,
-                                                   const uint8_t *__restrict__ edge_h,
-                                                   const uint8_t *__restrict__ perm) {
-  // index maps of the k edges at this lane's EPL entries
+// The index-map words of check c at a lane's EPL entries z0 .. z0 + EPL - 1: byte j of pw[e]
+// holds H_e (z0 + j) for edge e (they do not depend on the messages, so a caller may load the
+// next check's words while it works on the current one).
+template <int Q, int EPL, int KMAX>
+struct CheckIndex {
   uint32_t pw[KMAX][(EPL + 3) / 4];
+};
+template <int Q, int EPL, int KMAX>
+__device__ __forceinline__ void check_index_load(CheckIndex<Q, EPL, KMAX> &ix, int c, int k, int z0,
+                                                 const uint8_t *__restrict__ edge_h,
+                                                 const uint8_t *__restrict__ perm) {
+  auto &pw = ix.pw;
 #pragma unroll
   for (int e = 0; e < KMAX; ++e) {
     if (e < k) {
@@ -87,6 +92,13 @@ __device__ __forceinline__ void check_lane_inplace(W *s, int c, int k, int z0,
       }
     }
   }
+}
+
+// The lane's entries of check (slots at s[e * Q + z], Gamma form) in place, given its index words.
+// MAXG caps the gather group (1 for a caller whose register budget has no room for it).
+template <int Q, int EPL, int KMAX, typename W, int MAXG = EPL>
+__device__ __forceinline__ void check_lane_apply(W *s, int k, const CheckIndex<Q, EPL, KMAX> &ix) {
+  const auto &pw = ix.pw;
   // The words of a lane's entries are read and written by that lane alone, so a group of G
   // entries is gathered before any of them is written back: the compiler cannot prove that a
   // store of one entry misses the next entry's loads, and would otherwise serialise the entries.
@@ -148,6 +160,15 @@ __device__ __forceinline__ void check_lane_inplace(W *s, int c, int k, int z0,
       for (int g = 0; g < G; ++g) check_entry_store<Q, KMAX, W>(s, k, x[g], pos[g]);
     }
   }
+}
+
+template <int Q, int EPL, int KMAX, typename W, int MAXG = EPL>
+__device__ __forceinline__ void check_lane_inplace(W *s, int c, int k, int z0,
+                                                   const uint8_t *__restrict__ edge_h,
+                                                   const uint8_t *__restrict__ perm) {
+  CheckIndex<Q, EPL, KMAX> ix;
+  check_index_load<Q, EPL, KMAX>(ix, c, k, z0, edge_h, perm);
+  check_lane_apply<Q, EPL, KMAX, W, MAXG>(s, k, ix);
 }
 
 }  // namespace nbfd
