@@ -531,6 +531,21 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
                  ((l & 8) ? pw(7) : 0);
   const int xl1 = (l & 3) | ((l >> 2) & 3) << 6;
   const unsigned half_mask = sub ? 0xffff0000u : 0x0000ffffu;
+  // Tables that do not change across iterations, loaded once for the warp's first check, unit
+  // and stop-test check (each warp has one of each when N <= 2 * 16 * 16): the index words of
+  // its check, the edges of its unit's variable, the labels and variables of its stop-test edges.
+  CheckIndex<kQ, 8, KMAX> ix0;
+  if (gwarp < M) check_index_load<kQ, 8, KMAX>(ix0, gwarp, k, 8 * lane, edge_h, perm);
+  int2 e0 = make_int2(0, 0);
+  if (gwarp < units) {
+    const int v = 2 * gwarp + sub < N ? 2 * gwarp + sub : 2 * gwarp;
+    e0 = __ldg(reinterpret_cast<const int2 *>(var_edges) + v);
+  }
+  int sv0 = 0, sh0 = 0;  // stop test, first check: variable and label of edge `lane`
+  if (cbeg + wib < cend && lane < k) {
+    sv0 = __ldg(edge_var + (cbeg + wib) * k + lane);
+    sh0 = __ldg(edge_h + (cbeg + wib) * k + lane);
+  }
   // CHECK TO VARIABLE: one check per warp tile, lane entries z = 8 lane .. 8 lane + 7
   auto check_phase = [&]() {
     for (int c = gwarp; c < M; c += nwarp) {
@@ -538,7 +553,9 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
       float4 *t4 = reinterpret_cast<float4 *>(wm.tile);
       for (int i = lane; i < k * (kQ / 4); i += 32) t4[i] = __ldcg(src + i);
       __syncwarp();
-      check_lane_inplace<kQ, 8, KMAX, float, 1>(wm.tile, c, k, 8 * lane, edge_h, perm);
+      CheckIndex<kQ, 8, KMAX> ix = ix0;
+      if (c != gwarp) check_index_load<kQ, 8, KMAX>(ix, c, k, 8 * lane, edge_h, perm);
+      check_lane_apply<kQ, 8, KMAX, float, 1>(wm.tile, k, ix);
       __syncwarp();
       float4 *dst = reinterpret_cast<float4 *>(c2v + (fE + (size_t)c * k) * kQ);
       for (int i = lane; i < k * (kQ / 4); i += 32) dst[i] = t4[i];
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
     for (int u = gwarp; u < units; u += nwarp) {
       const bool valid = 2 * u + sub < N;
       const int v = valid ? 2 * u + sub : 2 * u;  // a stand-in computes and stores nothing
-      const int2 e = __ldg(reinterpret_cast<const int2 *>(var_edges) + v);
+      const int2 e = u == gwarp ? e0 : __ldg(reinterpret_cast<const int2 *>(var_edges) + v);
       const float4 *m1 = reinterpret_cast<const float4 *>(c2v + (fE + e.x) * kQ);
       const float4 *m2 = reinterpret_cast<const float4 *>(c2v + (fE + e.y) * kQ);
       float4 *d1 = reinterpret_cast<float4 *>(wm.v.msg[sub][0]);
@@ -584,9 +601,10 @@ __global__ void __launch_bounds__(32 * kTailWarps, 1)
       hv = 0;
       if (cs < cend && lane < k) {
         const int ed = cs * k + lane;
+        const bool first = cs == cbeg + wib;
         fb = __ldcg(fsyn + fE + ed);
-        xv = __ldcg(sym + (size_t)f * N + __ldg(edge_var + ed));
-        hv = __ldg(edge_h + ed);
+        xv = __ldcg(sym + (size_t)f * N + (first ? sv0 : __ldg(edge_var + ed)));
+        hv = first ? sh0 : __ldg(edge_h + ed);
       }
     };
     stop_load(cbeg + wib);
