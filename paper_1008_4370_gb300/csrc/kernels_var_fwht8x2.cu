@@ -54,15 +54,21 @@ __host__ __device__ constexpr int roff1(int j) {
 }
 static_assert(roff0(15) + roff1(15) < kBuf, "buffer");
 
+// buf[stage][variable] first holds the variable's two check messages (bulk-copy targets, edge 1
+// then edge 2), then -- once they are decoded into registers -- its transpose buffer and at the
+// end M in natural order. Sharing the space keeps a warp at 9 KB, so 5 blocks of 4 warps fit an SM.
 template <typename W, int S>
 struct X2Stage {
-  W msg[S][2][2][kQ];           // [stage][variable][edge 1, edge 2][z], bulk-copy targets
+  float2 buf[S][2][kBuf];       // [stage][variable]
   float llr[S][2][8];           // [stage][variable][bit]
-  float2 scratch[2][kBuf];      // [variable] transpose buffer; at the end M in natural order
   int4 idx[S][2];               // [stage][variable] = (frame, variable, slot e1, slot e2)
   float2 pbt[2][8];             // [variable][bit] = (Pr(b = 0), Pr(b = 1))
   uint64_t bar[S];
+  __device__ W *msg(int st, int h, int j) {
+    return reinterpret_cast<W *>(&buf[st][h][0]) + j * kQ;
+  }
 };
+static_assert(sizeof(float2) * kBuf >= 2 * kQ * sizeof(float), "messages fit the buffer");
 
 __device__ __forceinline__ void bfly(float2 &a, float2 &b) {
   const float2 s = __fadd2_rn(a, b);
@@ -186,6 +192,9 @@ __device__ __forceinline__ void x2_unit(const W *msg0, const W *msg1, const floa
     c[4 * g + 2] = make_float2(az.x, dz.x);
     c[4 * g + 3] = make_float2(az.y, dz.y);
   }
+  // the transpose buffer may be the messages' own (the variable-node kernel): every lane has read
+  // its entries before any lane writes
+  __syncwarp();
   // forward transforms of the pair (q x-domain check messages), P0 -> P1
   stages4(c);
   transpose<true>(c, sbuf, o0, o1);
@@ -370,8 +379,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
       ws.idx[st][h] = pf[h];
       if (h < pf_n) {
         const int4 ix = pf[h];
-        bulk_load(ws.msg[st][h][0], c2v + ((size_t)ix.x * E + ix.z) * kQ, vb, &ws.bar[st]);
-        bulk_load(ws.msg[st][h][1], c2v + ((size_t)ix.x * E + ix.w) * kQ, vb, &ws.bar[st]);
+        bulk_load(ws.msg(st, h, 0), c2v + ((size_t)ix.x * E + ix.z) * kQ, vb, &ws.bar[st]);
+        bulk_load(ws.msg(st, h, 1), c2v + ((size_t)ix.x * E + ix.w) * kQ, vb, &ws.bar[st]);
         bulk_load(ws.llr[st][h], llr + ((size_t)ix.x * N + ix.y) * 8, 32u, &ws.bar[st]);
       }
     }
@@ -394,7 +403,6 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
                  ((l & 8) ? pw(7) : 0);
   // lane part of x in P1 (lanes hold x0, x1, x6, x7)
   const int xl1 = (l & 3) | ((l >> 2) & 3) << 6;
-  float2 *sbuf = ws.scratch[sub];
   const unsigned half_mask = sub ? 0xffff0000u : 0x0000ffffu;
   long long t = 0;
   bool failed = false;
@@ -414,8 +422,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     const bool valid = item < total;
     const int4 ix = ws.idx[b][sub];
     const int f = ix.x, v = ix.y, e1 = ix.z, e2 = ix.w;
-    x2_unit<SYMBOL, W>(ws.msg[b][sub][0], ws.msg[b][sub][1], ws.llr[b][sub], ws.pbt[sub], sbuf,
-                       reinterpret_cast<float *>(ws.scratch), f, v, e1, e2, valid, v2c, sym, fsyn,
+    x2_unit<SYMBOL, W>(ws.msg(b, sub, 0), ws.msg(b, sub, 1), ws.llr[b][sub], ws.pbt[sub],
+                       ws.buf[b][sub], reinterpret_cast<float *>(ws.buf[b]), f, v, e1, e2, valid,
+                       v2c, sym, fsyn,
                        edge_z, N, E, lane, sub, l, o0, o1, xl1, half_mask);
     __syncwarp();
   }
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
 
 namespace {
 // launch shape: warps per block, pipeline depth, blocks per SM
-constexpr int kX2Warps = 4, kX2Stages = 2, kX2MinBlocks = 4;
+constexpr int kX2Warps = 4, kX2Stages = 2, kX2MinBlocks = 5;
 template <typename W>
 constexpr size_t x2_smem() {
   return sizeof(X2Stage<W, kX2Stages>) * kX2Warps;
