@@ -49,14 +49,19 @@ __host__ __device__ constexpr int roff1(int j) {  // P1: registers hold x2, x3, 
 }
 static_assert(roff0(15) + w6(2) + w6(3) < kVar && roff1(15) + w6(0) + w6(1) < kVar, "buffer");
 
+// buf[stage] first holds the unit's check messages ([variable][edge 1 | edge 2 | pad], bulk-copy
+// targets), then -- once they are decoded into registers -- the transposes, M in single floats
+// and M in natural order. Sharing the space keeps a warp at 10.5 KB (5 blocks of 4 warps per SM).
+constexpr int kStageFloats = 2 * 8 * kVar;  // the transpose buffers, >= 8 variables' messages
+static_assert(8 * kMsgStride <= kStageFloats && 8 * kNat <= kStageFloats, "stage buffer");
 template <int S>
 struct X8Stage {
-  float msg[S][8][kMsgStride];  // [stage][variable][edge 1 | edge 2 | pad], bulk-copy targets
+  float buf[S][kStageFloats];   // [stage]
   float llr[S][8 * 6];          // [stage] LLR rows of the unit's 8 variables
-  float2 scratch[8 * kVar];     // transposes; M in single floats; M in natural order at the end
   int4 idx[S][8];               // [stage][variable] = (frame, variable, slot e1, slot e2)
   float2 pbt[8][6];             // [variable][bit] = (Pr(b = 0), Pr(b = 1))
   uint64_t bar[S];
+  __device__ float *msg(int st, int g) { return &buf[st][g * kMsgStride]; }
 };
 
 __device__ __forceinline__ void bfly(float2 &a, float2 &b) {
@@ -136,8 +141,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     if (lane < 8) {
       const int2 e = pf_e;
       ws.idx[st][lane] = make_int4(f, v0 + lane, e.x, e.y);
-      bulk_load(&ws.msg[st][lane][0], c2v + ((size_t)f * E + e.x) * kQ6, kQ6 * 4u, &ws.bar[st]);
-      bulk_load(&ws.msg[st][lane][kQ6], c2v + ((size_t)f * E + e.y) * kQ6, kQ6 * 4u, &ws.bar[st]);
+      bulk_load(ws.msg(st, lane), c2v + ((size_t)f * E + e.x) * kQ6, kQ6 * 4u, &ws.bar[st]);
+      bulk_load(ws.msg(st, lane) + kQ6, c2v + ((size_t)f * E + e.y) * kQ6, kQ6 * 4u, &ws.bar[st]);
     } else if (lane == 8) {
       bulk_load(ws.llr[st], llr + ((size_t)f * N + v0) * 6, 8u * 6u * 4u, &ws.bar[st]);
     }
@@ -157,8 +162,6 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   // per-lane transpose offsets: P0 lanes hold x2, x3; P1 lanes hold x0, x1
   const int o0 = g * kVar + ((l & 1) ? w6(2) : 0) + ((l & 2) ? w6(3) : 0);
   const int o1 = g * kVar + ((l & 1) ? w6(0) : 0) + ((l & 2) ? w6(1) : 0);
-  float2 *sb2 = ws.scratch;
-  float *sb1 = reinterpret_cast<float *>(ws.scratch);
   long long t = 0;
   bool failed = false;
   for (; t < n_units; ++t) {
@@ -177,6 +180,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
       failed = true;
       break;
     }
+    float2 *sb2 = reinterpret_cast<float2 *>(ws.buf[b]);
+    float *sb1 = ws.buf[b];
     const int4 ix = ws.idx[b][g];
     const int f = ix.x, v = ix.y, e1 = ix.z, e2 = ix.w;
     // TENTATIVE read-out points of this lane, loaded now and used at the end: 18 per variable,
@@ -208,8 +213,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     float2 c[16];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 a = *reinterpret_cast<const float4 *>(&ws.msg[b][g][4 * l + 16 * q]);
-      const float4 d = *reinterpret_cast<const float4 *>(&ws.msg[b][g][kQ6 + 4 * l + 16 * q]);
+      const float4 a = *reinterpret_cast<const float4 *>(ws.msg(b, g) + 4 * l + 16 * q);
+      const float4 d = *reinterpret_cast<const float4 *>(ws.msg(b, g) + kQ6 + 4 * l + 16 * q);
       // packed pairs along the 16-byte loads (aligned register pairs)
       const float2 ax = gamma_decode2_ftz(a.x, a.y), az = gamma_decode2_ftz(a.z, a.w);
       const float2 dx = gamma_decode2_ftz(d.x, d.y), dz = gamma_decode2_ftz(d.z, d.w);
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
       c[4 * q + 2] = make_float2(az.x, dz.x);
       c[4 * q + 3] = make_float2(az.y, dz.y);
     }
+    __syncwarp();  // every lane has read its messages before the transposes reuse their space
     // forward transforms of the pair, P0 -> P1
     stage<0>(c);
     stage<1>(c);
@@ -375,14 +381,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
 }
 
 namespace {
-// Block shapes: (warps per block, resident blocks per SM). A warp holds 15.1 KB of shared memory
-// (two pipeline stages of 8 variables' messages, the transpose buffers), so an SM holds at most
-// 15 warps: 4-warp blocks fit 3 per SM (12 warps), 7-warp blocks 2 (14), one 15-warp block 15.
-// Registers are bounded to match (144, 144, 136 per thread).
+// Block shapes: (warps per block, resident blocks per SM). A warp holds 10.5 KB of shared memory
+// (two pipeline stages of 8 variables' messages, which the transposes reuse): 4-warp blocks fit
+// 5 per SM (20 warps, at most 102 registers), 7-warp blocks 2 (14), one 15-warp block 15.
 constexpr int kX8Stages = 2;
 constexpr int kX8DefaultWarps = 4;
 template <int W>
-constexpr int x8_min_blocks() { return W == 4 ? 3 : (W == 7 ? 2 : 1); }
+constexpr int x8_min_blocks() { return W == 4 ? 5 : (W == 7 ? 2 : 1); }
 template <int W>
 constexpr size_t x8_smem() { return sizeof(X8Stage<kX8Stages>) * W; }
 }  // namespace
@@ -416,10 +421,10 @@ cudaError_t launch_var_fwht6x8(const nbfd_code *c, FrameSet fs, const float *llr
                                float *v2c, uint16_t *sym, uint8_t *fsyn, int32_t *err,
                                cudaStream_t s, bool symbol, VarTune tune) {
   if (!var_fwht6x8_applies(c)) return cudaErrorInvalidValue;
-  // default shape: one 15-warp block per SM once every warp gets 64 units or more (measured 6%
-  // faster than 4-warp blocks at 2048 and 4096 GF(64) N=1200 frames, 3% slower at 512)
-  const long long units = (long long)fs.n_static * c->N / 8;
-  const int dflt = units >= (long long)sm_count() * 15 * 64 ? 15 : kX8DefaultWarps;
+  // default shape: 4-warp blocks, 5 per SM (measured with CUDA events at 2048 / 4096 GF(64) N=1200
+  // frames: 0.484 / 0.952 ms, against 0.517 / 0.992 ms for one 15-warp block per SM); the
+  // autotuner also times the 7- and 15-warp shapes
+  const int dflt = kX8DefaultWarps;
   switch (tune.warps > 0 ? tune.warps : dflt) {
     case 7:
       return launch_x8_shape<7>(c, fs, llr, c2v, v2c, sym, fsyn, err, s, symbol, tune.blocks_per_sm);
