@@ -38,8 +38,11 @@ __global__ void __launch_bounds__(kT4)
   const long long start = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   float *my_m = m_sh + threadIdx.x * kMStride;
+  const bool narrow = total < (1ll << 32);  // the usual case: 32-bit division
   for (long long item = start; item < total; item += stride) {
-    const long long slot = item / N;
+    const long long slot =
+        narrow ? static_cast<long long>(static_cast<uint32_t>(item) / static_cast<uint32_t>(N))
+               : item / N;
     const int v = static_cast<int>(item - slot * N);
     const int f = fs.list ? __ldg(fs.list + slot) : static_cast<int>(slot);
     const int2 e = __ldg(reinterpret_cast<const int2 *>(var_edges) + v);
