@@ -46,9 +46,9 @@ FORMS = {"direct": 0, "bf16": 1, "fp16": 2, "fwht": 3, "tc32": 4}
 #          --fused-steps 0 --table1-reps 0 --serve-mix-loads
 MEASURED_TRAFFIC = {
     ("var", "fwht", "gf256_n512_k4"): {
-        "bytes_per_frame": (272749824 + 219516160) / 256,
+        "bytes_per_frame": (272727552 + 218864896) / 256,
         "sources": ["kernels_var_fwht8x2.cu", "check_math.cuh", "device_common.cuh", "bulk_copy.cuh"],
-        "sha256_16": "642f4ccd31809670"},
+        "sha256_16": "4da423fecc9f612f"},
     ("check", "fwht", "gf256_n512_k4"): {
         "bytes_per_frame": (268656128 + 216033024) / 256,
         "sources": ["kernels_check.cu", "check_math.cuh", "device_common.cuh", "bulk_copy.cuh"],
