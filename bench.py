@@ -101,6 +101,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=16384, help="requests of the serving leg (0: skip)")
     ap.add_argument("--serve-load", type=float, default=30000.0, help="Poisson offered load, frames/s")
     ap.add_argument("--serve-sweep", action="store_true", help="serving sweep over loads and the code mix")
+    ap.add_argument("--serve-sweep-requests", type=int, default=100000, help="requests per load of the sweep")
     ap.add_argument("--serve-mix-loads", type=float, nargs="*", default=[1e4, 1e5],
                     help="offered loads (frames/s) of the five-code serving mix in the default run")
     return ap.parse_args()
@@ -563,12 +564,15 @@ def serve_mix_codes(nb):
     return codes
 
 
-def serve_mix_point(nb, codes, form, lam, dur):
-    """One offered load of the serving configuration: Poisson arrivals at lam frames/s for dur s,
-    each request a single frame of one of five codes (weights .1/.3/.2/.3/.1), per-request Eb/N0
-    uniform in 1.5-3.5 dB, max 100 iterations, a 40 GB budget for resident messages."""
+def serve_mix_point(nb, codes, form, lam, n_req, pool_frames=8192):
+    """One offered load of the serving configuration: n_req Poisson arrivals at lam frames/s, each
+    request a single frame of one of five codes (weights .1/.3/.2/.3/.1), per-request Eb/N0
+    uniform in 1.5-3.5 dB, max 100 iterations, a 40 GB budget for resident messages. Each code's
+    requests draw from a pool of up to pool_frames distinct frames (each with its own Eb/N0), so
+    that long runs need not synthesise every frame; requests beyond the pool reuse its frames in
+    order."""
     rng = synth.rng_for(17, int(lam))
-    n_req = int(lam * dur)
+    dur = n_req / lam
     arr = np.sort(rng.uniform(0.0, dur, size=n_req))
     which = rng.choice(len(SERVE_MIX), size=n_req, p=[w for _, w in SERVE_MIX])
     streams = []
@@ -577,11 +581,15 @@ def serve_mix_point(nb, codes, form, lam, dur):
         if len(sel) == 0:
             continue
         c, code, bits, enc = codes[name]
-        ebn0 = rng.uniform(1.5, 3.5, size=len(sel))
-        _, llr = synth.frames(c, len(sel), ebn0, snr_idx=ci, batch_idx=int(lam) % 100000, encoder=enc)
+        n_pool = min(len(sel), pool_frames)
+        ebn0 = rng.uniform(1.5, 3.5, size=n_pool)
+        _, pool = synth.frames(c, n_pool, ebn0, snr_idx=ci, batch_idx=int(lam) % 100000, encoder=enc)
+        llr = pool if n_pool == len(sel) else np.ascontiguousarray(pool[np.arange(len(sel)) % n_pool])
         streams.append((code, llr, arr[sel], 100, bits))
     got, wall, ph = serve_run(nb, streams, form, 40 << 30)
-    return serve_summary(got, wall, ph, lam)
+    out = serve_summary(got, wall, ph, lam)
+    out["distinct_frames"] = int(sum(min(int(np.sum(which == ci)), pool_frames) for ci in range(len(SERVE_MIX))))
+    return out
 
 
 def run_serve_sweep(a):
@@ -596,8 +604,8 @@ def run_serve_sweep(a):
     codes = serve_mix_codes(nb)
     form = FORMS[a.form] if FORMS[a.form] in (0, 3) else FORMS["fwht"]
     for lam in [1e4, 3e4, 1e5, 3e5, 1e6]:
-        dur = min(1.0, max(0.2, 20000.0 / lam))
-        print(json.dumps({"serving_sweep": serve_mix_point(nb, codes, form, lam, dur), "form": a.form}), flush=True)
+        print(json.dumps({"serving_sweep": serve_mix_point(nb, codes, form, lam, a.serve_sweep_requests),
+                          "form": a.form}), flush=True)
 
 
 def run_ours(a):
@@ -786,7 +794,7 @@ def run_ours(a):
         if a.serve_mix_loads:
             # the configured five-code mix at a few offered loads (the full sweep: --serve-sweep)
             codes_mix = serve_mix_codes(nb)
-            served["mix"] = [serve_mix_point(nb, codes_mix, form, lam, min(1.0, max(0.2, 10000.0 / lam)))
+            served["mix"] = [serve_mix_point(nb, codes_mix, form, lam, int(lam * min(1.0, max(0.2, 10000.0 / lam))))
                              for lam in a.serve_mix_loads]
     peaks, peak_kind = load_peaks()
     gf64 = None
