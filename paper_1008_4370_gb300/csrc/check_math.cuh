@@ -66,11 +66,55 @@ template <int Q, int EPL, int KMAX>
 struct CheckIndex {
   uint32_t pw[KMAX][(EPL + 3) / 4];
 };
+// One edge's index-map word(s) from its label h.
+template <int Q, int EPL>
+__device__ __forceinline__ void check_index_row(uint32_t (&w)[(EPL + 3) / 4], int h, int z0,
+                                                const uint8_t *__restrict__ perm) {
+  const uint8_t *row = perm + h * Q + z0;
+  if constexpr (EPL == 8) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row));
+    w[0] = v.x;
+    w[1] = v.y;
+  } else if constexpr (EPL == 4) {
+    w[0] = __ldg(reinterpret_cast<const uint32_t *>(row));
+  } else if constexpr (EPL == 2) {
+    w[0] = __ldg(reinterpret_cast<const uint16_t *>(row));
+  } else {
+    uint32_t x = 0;
+#pragma unroll
+    for (int jj = 0; jj < EPL; ++jj) x |= (uint32_t)__ldg(row + jj) << (8 * jj);
+    w[0] = x;
+  }
+}
+
 template <int Q, int EPL, int KMAX>
 __device__ __forceinline__ void check_index_load(CheckIndex<Q, EPL, KMAX> &ix, int c, int k, int z0,
                                                  const uint8_t *__restrict__ edge_h,
                                                  const uint8_t *__restrict__ perm) {
   auto &pw = ix.pw;
+  if constexpr (KMAX == 4 || KMAX == 8 || KMAX == 16) {
+    if (k == KMAX) {  // the check's KMAX labels as one aligned 4-, 8- or 16-byte load
+      uint32_t hw[KMAX / 4];
+      const uint8_t *p = edge_h + (size_t)c * KMAX;
+      if constexpr (KMAX == 4) {
+        hw[0] = __ldg(reinterpret_cast<const uint32_t *>(p));
+      } else if constexpr (KMAX == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        hw[0] = v.x;
+        hw[1] = v.y;
+      } else {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        hw[0] = v.x;
+        hw[1] = v.y;
+        hw[2] = v.z;
+        hw[3] = v.w;
+      }
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e)
+        check_index_row<Q, EPL>(pw[e], (hw[e >> 2] >> (8 * (e & 3))) & 0xff, z0, perm);
+      return;
+    }
+  }
 #pragma unroll
   for (int e = 0; e < KMAX; ++e) {
     if (e < k) {
