@@ -246,8 +246,13 @@ def run_reference(a):
         "unit": "Mbit/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "GF(256) (2,4) N=512, Eb/N0 1.5 dB, max 100 iterations",
-                   "sample_frames_per_step": cores},
+        "config": {"workload": ("GF(256) (2,4) N=512, 1024 frames per step, Eb/N0 1.5 dB, random codewords, "
+                                "max 100 iterations, early stop") if a.frames == 1024 else
+                   f"{CODE_NAME}, {a.frames} frames per step, Eb/N0 {a.ebn0} dB, random codewords, "
+                   f"max {a.max_iter} iterations",
+                   "frames_per_step": a.frames, "ebn0_db": a.ebn0, "max_iter": a.max_iter,
+                   "form": "FP64 oracle (literal log-domain boxplus)", "info_bits_per_frame": info_bits,
+                   "sample_frames_per_step": cores, "parallelism": f"{cores} host processes"},
         "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": cores, "kind": "oracle",
                          "sample": f"{cores} frames x 1 iteration per step on {cores} processes; "
                                    f"converted at {it_mean:.2f} mean iterations per frame"},
