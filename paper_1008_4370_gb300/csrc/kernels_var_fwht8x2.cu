@@ -426,6 +426,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
                        ws.buf[b][sub], reinterpret_cast<float *>(ws.buf[b]), f, v, e1, e2, valid,
                        v2c, sym, fsyn,
                        edge_z, N, E, lane, sub, l, o0, o1, xl1, half_mask);
+    // every lane wrote this stage (transposes, M): its writes are ordered before the bulk copies
+    // that refill the stage (issued by lane 0 after this barrier)
+    fence_proxy_async_smem();
     __syncwarp();
   }
   if (failed && lane == 0) {
