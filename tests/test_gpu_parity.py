@@ -293,6 +293,17 @@ def test_fourier_only_clears_count(dev, form):
     print(f"fourier-only clears: {total} over 100 frames")
 
 
+@pytest.mark.parametrize("spec,ebn0", [((8, 64, 16, 27), 4.0), ((7, 40, 10, 29), 3.5)])
+def test_decode_parity_high_row_weight(dev, spec, ebn0):
+    """Whole decodes of codes whose check node runs the team variant (q >= 128, k > 8: a block's
+    warps share one pipeline of whole checks), random codewords, against the oracle's decodes."""
+    c = _code(spec)
+    _, llr = synth.frames(c, 24, ebn0, batch_idx=13)
+    sym, ok, it, n_sym, n_it = _decode_vs_oracle(dev, c, llr, 20, min_frac=0.5, form=nb.FORM_FP32_FWHT)
+    assert ok.any() and it.max() <= 20
+    print(f"\n{spec}: decoded {ok.mean():.3f}, {n_sym} frames compared, {n_it} iteration counts")
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_decode_parity_gf4_n8(dev, form):
     c = synth.named_code("gf4_n8_k4")
